@@ -1,0 +1,123 @@
+"""Brute-force and closed-form references that pin the oracle (test infrastructure).
+
+* Onsager's nearest-neighbour correlation of the 2D Ising model, reached by
+  the 'Ising PEPS' A[s,u,l,d,r] = Q[s,u] Q[s,l] Q[s,d] Q[s,r] with
+  Q Q^T = [[e^{K/2}, e^{-K/2}], [e^{-K/2}, e^{K/2}]], whose norm network is
+  the Ising partition function at coupling K.
+* The infinite cylinder of circumference W: the exact dominant eigenvectors of
+  the double-layer column transfer matrix (dimension D^(2W)) give the
+  bond density matrices; they approach the 2D (CTMRG) values as W grows.
+* Exact expectation values on small periodic tori by full contraction.
+
+None of these share code with the CTMRG oracle: they contract the
+network in a different order, from scratch.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import ellipk
+
+
+def ising_peps(K: float) -> np.ndarray:
+    W = np.array([[np.exp(K / 2), np.exp(-K / 2)], [np.exp(-K / 2), np.exp(K / 2)]])
+    w, v = np.linalg.eigh(W)
+    Q = v @ np.diag(np.sqrt(w)) @ v.T
+    return np.einsum("su,sl,sd,sr->suldr", Q, Q, Q, Q)
+
+
+def onsager_nn(K: float) -> float:
+    """<sigma_i sigma_j> for nearest neighbours of the square-lattice Ising
+    model (Onsager), with the modulus k = 2 sinh 2K / cosh^2 2K and the
+    complete elliptic integral K(k) (scipy takes the parameter m = k^2)."""
+    k = 2.0 * np.sinh(2 * K) / np.cosh(2 * K) ** 2
+    return 0.5 / np.tanh(2 * K) * (1.0 + (2.0 / np.pi) * (2.0 * np.tanh(2 * K) ** 2 - 1.0) * ellipk(k * k))
+
+
+def _site(A, kb=None):
+    """Double-layer site tensor a[(u u'), (l l'), (d d'), (r r')]; with kb = (k, b)
+    the physical legs are fixed to ket k and bra b instead of summed."""
+    D = A.shape[1]
+    if kb is None:
+        a = np.einsum("suldr,svmek->uvlmderk", A, A)
+    else:
+        k, b = kb
+        a = np.einsum("uldr,vmek->uvlmderk", A[k], A[b])
+    return a.reshape(D * D, D * D, D * D, D * D)
+
+
+def _column(sites):
+    """Column transfer matrix T[(l_1..l_W), (r_1..r_W)] of a periodic column
+    of double-layer tensors sites[i][u, l, d, r] (row i's d joins row i+1's u)."""
+    W = len(sites)
+    X = sites[0]                                    # [u1, l1, d1, r1]
+    X = X.reshape(X.shape[0], X.shape[1], X.shape[2], X.shape[3])
+    # X[u1, L, u_next, R] with L, R flattened
+    X = X.transpose(0, 1, 3, 2)                    # [u1, l1, r1, d1]
+    for i in range(1, W):
+        a = sites[i]                                # [u, l, d, r]
+        X = np.einsum("aLRu,ulds->aLlRsd", X, a)
+        s = X.shape
+        X = X.reshape(s[0], s[1] * s[2], s[3] * s[4], s[5])
+    T = np.einsum("aLRa->LR", X)
+    return T
+
+
+def cylinder_rdms(A, W):
+    """Exact horizontal and vertical two-site density matrices rho[k1, b1, k2, b2]
+    (trace one) on the infinite cylinder of circumference W (periodic in y)."""
+    d = A.shape[0]
+    a = _site(A)
+    T = _column([a] * W)
+    ev, vr = np.linalg.eig(T)
+    i = np.argmax(np.abs(ev))
+    lam = ev[i].real
+    vR = vr[:, i].real
+    evl, vl = np.linalg.eig(T.T)
+    j = np.argmax(np.abs(evl))
+    vL = vl[:, j].real
+    norm2 = vL @ T @ T @ vR
+    norm1 = vL @ T @ vR
+    rho_h = np.zeros((d, d, d, d))
+    rho_v = np.zeros((d, d, d, d))
+    Topen = {}
+    for k in range(d):
+        for b in range(d):
+            Topen[k, b] = _column([_site(A, (k, b))] + [a] * (W - 1))
+    for k1 in range(d):
+        for b1 in range(d):
+            left = vL @ Topen[k1, b1]
+            for k2 in range(d):
+                for b2 in range(d):
+                    rho_h[k1, b1, k2, b2] = left @ Topen[k2, b2] @ vR / norm2
+                    Tv = _column([_site(A, (k1, b1)), _site(A, (k2, b2))] + [a] * (W - 2))
+                    rho_v[k1, b1, k2, b2] = vL @ Tv @ vR / norm1
+    return rho_h, rho_v, lam
+
+
+def bond_energy(rho, h):
+    d = rho.shape[0]
+    hh = h.reshape(d, d, d, d)                       # [b1, b2, k1, k2]
+    return float(np.einsum("kbmc,bckm->", rho, hh) / np.einsum("kkmm->", rho))
+
+
+def torus_state(A, L):
+    """Amplitudes psi[s_1..s_{L*L}] of the uniform PEPS on an L x L torus
+    (sites ordered row-major by (y, x)); small L only."""
+    import itertools
+    cnt = itertools.count()
+
+    def sym():
+        return next(cnt)
+    hb = {(x, y): sym() for x in range(L) for y in range(L)}   # bond right of (x, y)
+    vb = {(x, y): sym() for x in range(L) for y in range(L)}   # bond below (x, y)
+    phys = {(x, y): sym() for x in range(L) for y in range(L)}
+    ops = []
+    for y in range(L):
+        for x in range(L):
+            u = vb[x, (y - 1) % L]
+            l = hb[(x - 1) % L, y]
+            dn = vb[x, y]
+            r = hb[x, y]
+            ops += [A, [phys[x, y], u, l, dn, r]]
+    out = [phys[x, y] for y in range(L) for x in range(L)]
+    return np.einsum(*ops, out, optimize="greedy")

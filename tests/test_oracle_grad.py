@@ -1,0 +1,61 @@
+"""Pins of the oracle's fixed-point gradient (Sec. III.A gradient; Sec. IV.A (n+N) scheme)."""
+import numpy as np
+import pytest
+
+from oracle import gradient as G
+from oracle import models
+from paper_2511_09546_gb300 import inputs
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    cell = inputs.WORKLOADS["heis_d2_chi16"]["gen"]()
+    ham = models.heisenberg(True)
+    E, g, info = G.energy_and_gradient(cell, ham, 16, tol=1e-12, return_info=True)
+    return cell, ham, E, g, info
+
+
+def test_fixed_point_and_adjoint_converge(cfg1):
+    _, _, _, _, info = cfg1
+    assert info["fixed_point_residual"] < 1e-8
+    assert info["adjoint_residual"] < 1e-12
+
+
+def test_scale_invariance(cfg1):
+    # E(cA) = E(A)  =>  <g, A> = 0
+    cell, _, _, g, _ = cfg1
+    assert abs(np.sum(g[0][0] * cell[0][0])) < 1e-10 * np.linalg.norm(g[0][0]) * np.linalg.norm(cell[0][0])
+
+
+def test_central_finite_differences(cfg1):
+    cell, ham, _, g, info = cfg1
+    A = cell[0][0]
+    h = 1e-6
+    idx = inputs.random_entries(A.size, 4, seed=1)
+    for i in idx:
+        vals = []
+        for sgn in (1, -1):
+            Ap = A.copy().ravel()
+            Ap[i] += sgn * h
+            E, _ = G.energy_at([[Ap.reshape(A.shape)]], ham, 16, tol=1e-12, maxit=400, env=info["env"])
+            vals.append(E)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - g[0][0].ravel()[i]) < 2e-8, (i, fd, g[0][0].ravel()[i])
+
+
+def test_product_state_gradient_vanishes():
+    # D=1 real spinors all have E = -1/2 in the rotated frame: g = 0
+    cell = inputs.product_state_cell(1, 1, [[0.8, -0.35]])
+    E, g = G.energy_and_gradient(cell, models.heisenberg(True), 1, tol=1e-13)
+    assert abs(E + 0.5) < 1e-13
+    assert np.max(np.abs(g[0][0])) < 1e-12
+
+
+def test_unrolled_converges_to_fixed_point(cfg1):
+    cell, ham, _, g, _ = cfg1
+    errs = []
+    for n in (2, 8, 32):
+        _, gu = G.unrolled_gradient(cell, ham, 16, n, tol=1e-12)
+        errs.append(np.linalg.norm(gu[0][0] - g[0][0]) / np.linalg.norm(g[0][0]))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 1e-6
