@@ -1,0 +1,174 @@
+/*
+ * ipeps.h -- C ABI of the GB300 (sm_103a) preconditioned iPEPS hot path.
+ *
+ * The library computes, for an iPEPS unit cell of real tensors,
+ *   - the CTMRG environment run to a fixed point (Sec. III.A of the paper:
+ *     the energy is contracted with CTMRG);
+ *   - the energy per site, Eq. (equ:energy), and its gradient dE/dA at the
+ *     fixed point (Sec. III.A: the gradient of the energy functional);
+ *   - the local-metric preconditioner, Eq. (equ:local_metric), regularised by
+ *     delta I (Sec. III.B) and inverted with GMRES (Sec. III.C);
+ *   - plain and preconditioned L-BFGS with the Hager-Zhang line search
+ *     (Sec. II and Sec. IV.A).
+ *
+ * Conventions shared by every call
+ *   - Tensor layout: the unit cell has Lx columns and Ly rows; tensor (x, y)
+ *     is stored at offset (x * Ly + y) * d * D^4 doubles, each tensor
+ *     row-major with legs (s, u, l, d, r) = (physical, up, left, down, right).
+ *   - Pointers named *_dev are device pointers owned by the caller; *_host
+ *     and scalar outputs are host pointers.  The library owns ipeps_env,
+ *     ipeps_ham and its workspaces (stream-ordered pool allocations).
+ *   - Every call is enqueued on `stream` (NULL = the legacy default stream)
+ *     and returns after the host scalars it reports are available, i.e. it
+ *     synchronises the stream before returning.
+ *   - Nothing aborts or traps: errors come back as an ipeps_status and a
+ *     thread-local message from ipeps_last_error().  Inputs are FP64; the
+ *     precision enum only selects the arithmetic of the bulk contractions.
+ *   - No call launches a kernel that waits on another launch.
+ */
+#ifndef IPEPS_H
+#define IPEPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IPEPS_OK = 0,
+  IPEPS_ERR_ARG = 1,           /* invalid argument (shape, size, NULL pointer) */
+  IPEPS_ERR_NOMEM = 2,         /* device allocation failed */
+  IPEPS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  IPEPS_ERR_NONFINITE = 4,     /* NaN or Inf in an input or produced value */
+  IPEPS_ERR_NOT_CONVERGED = 5, /* iteration limit reached; best result kept */
+  IPEPS_ERR_TIMEOUT = 6,       /* a bounded device wait ran out */
+  IPEPS_ERR_CANCELLED = 7      /* stopped by the caller's callback */
+} ipeps_status;
+
+typedef enum {
+  IPEPS_FP64 = 0,    /* every contraction in FP64 */
+  IPEPS_TF32X3 = 1   /* bulk contraction GEMMs as 3xTF32 on tcgen05 tensor cores,
+                        FP32 accumulate; projectors, normalisation, convergence,
+                        gradient adjoint and preconditioner stay FP64 */
+} ipeps_prec;
+
+typedef struct {
+  int Lx, Ly; /* unit cell: columns, rows (>= 1) */
+  int d;      /* physical dimension (>= 1) */
+  int D;      /* virtual bond dimension (>= 1) */
+} ipeps_shape;
+
+typedef struct CUstream_st *ipeps_stream_t; /* same type as cudaStream_t */
+typedef struct ipeps_env_s *ipeps_env;      /* opaque, device resident */
+typedef struct ipeps_ham_s *ipeps_ham;      /* opaque, host resident */
+
+/* ------------------------------------------------------------------ S0 */
+/* Dense Hamiltonian terms (host pointers, copied).  h_h: (d*d) x (d*d)
+ * operator on the horizontal bond (left site, right site); h_v: same on the
+ * vertical bond (upper site, lower site); h_site: d x d on-site term or NULL;
+ * scale multiplies the per-tensor energy to give the energy per site.
+ * Matrix element op[(b1*d + b2) * d*d + (k1*d + k2)] = <b1 b2|op|k1 k2>.
+ * Sec. IV.A Eq. (eq:H_heisenberg); Sec. IV.B. */
+ipeps_status ipeps_ham_create(int d, const double *h_h, const double *h_v,
+                              const double *h_site, double scale, ipeps_ham *out);
+/* Spin-1/2 Heisenberg S.S (J); rotated != 0 applies the sublattice spin flip
+ * of Sec. IV.A (second site rotated by i sigma_y), as used with a 1x1 cell. */
+ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out);
+/* Spin-1/2 Kitaev model K S^g S^g with two sites (a, b) merged per tensor
+ * (d = 4): z link inside the tensor, x link b(x,y)-a(x+1,y), y link
+ * b(x,y)-a(x,y+1); energy reported per honeycomb site (scale 1/2). */
+ipeps_status ipeps_ham_kitaev(double K, ipeps_ham *out);
+void ipeps_ham_destroy(ipeps_ham h);
+
+/* --------------------------------------------------------- S1 .. S6 */
+/* CTMRG environment to a fixed point (Sec. III.A).  A_dev: the unit cell
+ * (layout above).  chi: environment bond dimension (>= 1).  Iterates until
+ * the largest change of the normalised corner singular values is < tol, or
+ * maxit iterations.  *inout_env == NULL: cold start, a new environment is
+ * created and returned; otherwise it is warm started (it must have the same
+ * shape and chi).  iters_out / err_out (host, may be NULL) receive the
+ * iteration count and the final change.  Returns IPEPS_ERR_NOT_CONVERGED
+ * (environment kept) when maxit is reached. */
+ipeps_status ipeps_ctmrg(const ipeps_shape *shape, const double *A_dev, int chi, double tol,
+                         int maxit, ipeps_prec prec, ipeps_env *inout_env, int *iters_out,
+                         double *err_out, ipeps_stream_t stream);
+
+/* Normalised singular values of the 4*Lx*Ly corners, chi each, written to
+ * host memory (4*Lx*Ly*chi doubles, corner order C1..C4, site order x*Ly+y).
+ * Gauge invariant; used to compare environments. */
+ipeps_status ipeps_env_corner_spectra(ipeps_env env, double *out_host, size_t n,
+                                      ipeps_stream_t stream);
+void ipeps_env_destroy(ipeps_env env);
+
+/* ------------------------------------------------------------ S7 .. S10 */
+/* Energy per site, Eq. (equ:energy), from a converged environment. */
+ipeps_status ipeps_energy(const ipeps_shape *shape, const double *A_dev, ipeps_env env,
+                          ipeps_ham ham, double *E_out, ipeps_stream_t stream);
+/* Energy and its gradient dE/dA at the CTMRG fixed point (Sec. III.A),
+ * differentiated implicitly: g = dE/dA|_env + (dF/dA)^T lam with
+ * (I - (dF/denv)^T) lam = dE/denv, F one gauge-fixed CTMRG iteration.
+ * env must be converged for A_dev.  grad_dev: caller-allocated device
+ * buffer with the layout of A.  E_out: host. */
+ipeps_status ipeps_energy_grad(const ipeps_shape *shape, const double *A_dev, ipeps_env env,
+                               ipeps_ham ham, double *E_out, double *grad_dev,
+                               ipeps_stream_t stream);
+
+/* ------------------------------------------------------------ S11, S12 */
+/* Preconditioned gradient P^-1 g for every tensor of the cell:
+ * P = 1_d (x) M + delta I with M the tensor's single-site environment
+ * (Eq. equ:local_metric; Sec. IV.B: one M per tensor), symmetrised and
+ * scaled so that <A|1 (x) M|A> = 1; solved by GMRES with Krylov dimension
+ * `krylov` and `restarts` outer iterations, x0 = 0 (Sec. III.C uses 30 and
+ * 1).  g_dev, out_dev: device, layout of A (out_dev may alias nothing).
+ * resid_out (host, may be NULL): the largest relative residual. */
+ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, ipeps_env env,
+                                const double *g_dev, double delta, int krylov, int restarts,
+                                double *out_dev, double *resid_out, ipeps_stream_t stream);
+
+/* ----------------------------------------------------------------- S13 */
+typedef struct {
+  int chi;              /* environment bond dimension */
+  double ctm_tol;       /* CTMRG corner-spectrum tolerance */
+  int ctm_maxit;        /* CTMRG iteration limit per evaluation */
+  ipeps_prec prec;      /* contraction arithmetic */
+  int precondition;     /* 0: plain L-BFGS, 1: local-metric preconditioned */
+  int krylov, restarts; /* GMRES (30, 1 in Sec. III.C) */
+  int delta_rule;       /* 0: delta = |g|^2, 1: delta = |E_k - E_{k-1}| (Sec. III.B) */
+  int history;          /* L-BFGS history m (200 in Sec. IV.A) */
+  int maxiter;          /* optimisation iterations */
+  double gtol;          /* stop when |g| < gtol */
+  double E_target;      /* stop when E <= E_target (use -1e300 to disable) */
+} ipeps_opts;
+
+typedef struct {
+  int iter;        /* 0 for the starting point */
+  double E;        /* energy per site */
+  double gnorm;    /* |g| */
+  double alpha;    /* accepted step (0 for iter 0) */
+  double delta;    /* regularisation used for the step */
+  int evals;       /* energy/gradient evaluations of this iteration */
+  int ctm_iters;   /* CTMRG iterations of the accepted point */
+  double wall_ms;  /* wall time of the iteration */
+} ipeps_iter_info;
+
+/* Return nonzero from the callback to stop (status IPEPS_ERR_CANCELLED). */
+typedef int (*ipeps_iter_cb)(const ipeps_iter_info *info, void *user);
+
+void ipeps_opts_default(ipeps_opts *opts);
+/* Minimise E(A) (Sec. II, Sec. IV.A).  A_dev: in the starting cell, out the
+ * final cell.  cb may be NULL. */
+ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham ham,
+                            const ipeps_opts *opts, ipeps_iter_cb cb, void *user,
+                            ipeps_stream_t stream);
+
+/* ------------------------------------------------------------- misc */
+const char *ipeps_last_error(void);
+/* Kernel launches issued by this thread since the last reset (for reports). */
+uint64_t ipeps_launch_count(int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IPEPS_H */

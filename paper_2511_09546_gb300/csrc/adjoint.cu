@@ -1,0 +1,123 @@
+// Energy and its gradient at the CTMRG fixed point (Sec. III.A: dE/dA of the
+// energy functional), by implicit differentiation of the fixed point.
+//
+// With F one CTMRG iteration followed by the constant sign gauge sigma that
+// makes the converged environment e* an elementwise fixed point,
+//   g = dE/dA|_e + (dF/dA)^T lam,   (I - (dF/de)^T) lam = dE/de|_A.
+// One F pass and one energy pass are recorded on tapes (their intermediates
+// stay resident in HBM); every Krylov step of the device GMRES replays the
+// hand-written adjoints of the F tape with a new cotangent.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.h"
+#include "engine.h"
+#include "ipeps_impl.h"
+#include "kernels.h"
+
+namespace ipeps {
+
+double energy_only(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl &H, cudaStream_t s) {
+  HamDev hd(H, s);
+  Tape t(s);
+  t.record = false;
+  StateVars sv = state_leaves(t, e, A_dev);
+  int E = energy_on_tape(t, c, e.chi, sv, H, hd);
+  double v;
+  IPEPS_CUDA(cudaMemcpyAsync(&v, t.vp(E), sizeof(double), cudaMemcpyDeviceToHost, s));
+  IPEPS_CUDA(cudaStreamSynchronize(s));
+  return v;
+}
+
+double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl &H, double *grad,
+                   cudaStream_t s, double *adj_resid, int *adj_mv, double *fp_resid) {
+  const int ns = c.nsites();
+  const int64_t nenv = e.total(), ta = c.tsize();
+  HamDev hd(H, s);
+
+  // ---- F tape at e*
+  Tape tF(s);
+  StateVars in = state_leaves(tF, e, A_dev);
+  StateVars out = in;
+  ctmrg_iteration(tF, c, e.chi, out);
+  std::vector<const double *> cand(8 * ns);
+  for (int n = 0; n < 8; ++n)
+    for (int i = 0; i < ns; ++i) cand[n * ns + i] = tF.vp(out.env[n][i]);
+  double fpres = 0.0;
+  DBuf sig = solve_signs(e, cand, s, &fpres);
+  std::vector<int> outs(8 * ns);
+  for (int n = 0; n < 8; ++n)
+    for (int i = 0; i < ns; ++i) {
+      int k = n * ns + i;
+      outs[k] = t_signs(tF, out.env[n][i], sig.p + int64_t(2 * k) * e.chi, sig.p + int64_t(2 * k + 1) * e.chi);
+    }
+  if (fp_resid) *fp_resid = fpres;
+
+  // ---- energy tape: E, dE/de, dE/dA
+  Tape tE(s);
+  StateVars se = state_leaves(tE, e, A_dev);
+  int Ev = energy_on_tape(tE, c, e.chi, se, H, hd);
+  fill(tE.grad(Ev), 1, 1.0, s);
+  tE.backward();
+  double E;
+  IPEPS_CUDA(cudaMemcpyAsync(&E, tE.vp(Ev), sizeof(double), cudaMemcpyDeviceToHost, s));
+  DBuf ebar(size_t(nenv), s);
+  fill(ebar.p, nenv, 0.0, s);
+  for (int n = 0; n < 8; ++n)
+    for (int i = 0; i < ns; ++i) {
+      double *g = tE.grad(se.env[n][i], false);
+      if (g)
+        IPEPS_CUDA(cudaMemcpyAsync(ebar.p + e.offset(n, i / c.Ly, i % c.Ly), g,
+                                   tE.val(se.env[n][i]).size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
+  fill(grad, int64_t(ns) * ta, 0.0, s);
+  for (int i = 0; i < ns; ++i) {
+    double *g = tE.grad(se.A[0][i], false);
+    if (g) axpy(ta, 1.0, g, grad + int64_t(i) * ta, s);
+  }
+  tE.clear();
+
+  // ---- vector-Jacobian products of F
+  auto vjp = [&](const double *lam, double *out_env, double *out_A) {
+    tF.zero_grads();
+    for (int n = 0; n < 8; ++n)
+      for (int i = 0; i < ns; ++i) {
+        int k = n * ns + i;
+        IPEPS_CUDA(cudaMemcpyAsync(tF.grad(outs[k]), lam + e.offset(n, i / c.Ly, i % c.Ly),
+                                   tF.val(outs[k]).size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      }
+    tF.backward();
+    if (out_env) {
+      fill(out_env, nenv, 0.0, s);
+      for (int n = 0; n < 8; ++n)
+        for (int i = 0; i < ns; ++i) {
+          double *g = tF.grad(in.env[n][i], false);
+          if (g)
+            IPEPS_CUDA(cudaMemcpyAsync(out_env + e.offset(n, i / c.Ly, i % c.Ly), g,
+                                       tF.val(in.env[n][i]).size() * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, s));
+        }
+    }
+    if (out_A)
+      for (int i = 0; i < ns; ++i) {
+        double *g = tF.grad(in.A[0][i], false);
+        if (g) axpy(ta, 1.0, g, out_A + int64_t(i) * ta, s);
+      }
+  };
+  MatVec mv = [&](const double *x, double *y) {
+    vjp(x, y, nullptr);
+    axpby(nenv, 1.0, x, -1.0, y, s);  // y = x - J^T x
+  };
+  DBuf lam(size_t(nenv), s);
+  int nmv = 0;
+  double rel = gmres_dev(nenv, mv, ebar.p, lam.p, 40, 12, 1e-12, s, &nmv);
+  vjp(lam.p, nullptr, grad);
+  IPEPS_CUDA(cudaStreamSynchronize(s));
+  if (adj_resid) *adj_resid = rel;
+  if (adj_mv) *adj_mv = nmv;
+  return E;
+}
+
+}  // namespace ipeps

@@ -1,0 +1,339 @@
+// C ABI of libipeps (include/ipeps.h): argument checks, error translation and
+// the runtime helpers shared by the translation units.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "../../include/ipeps.h"
+#include "common.h"
+#include "ipeps_impl.h"
+#include "kernels.h"
+
+struct ipeps_env_s {
+  ipeps::EnvImpl impl;
+};
+struct ipeps_ham_s {
+  ipeps::HamImpl impl;
+};
+
+namespace ipeps {
+
+ipeps_status optimize_impl(const Cell &c, double *A_dev, const HamImpl &H, const ipeps_opts &o,
+                           ipeps_iter_cb cb, void *user, cudaStream_t s);
+
+uint64_t &launch_counter() {
+  static thread_local uint64_t n = 0;
+  return n;
+}
+
+void check_launch(const char *what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) throw Error(IPEPS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  static bool pool_ready = false;
+  if (!pool_ready) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t keep = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+    pool_ready = true;
+  }
+  void *p = nullptr;
+  if (bytes == 0) bytes = 8;
+  cudaError_t e = cudaMallocAsync(&p, bytes, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Error(IPEPS_ERR_NOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  return p;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+}  // namespace ipeps
+
+namespace {
+thread_local std::string g_last_error;
+
+template <class F>
+ipeps_status guarded(F &&f) {
+  try {
+    return f();
+  } catch (const ipeps::Error &e) {
+    g_last_error = e.what();
+    return e.code;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return IPEPS_ERR_CUDA;
+  }
+}
+
+ipeps::Cell cell_of(const ipeps_shape *sh) {
+  IPEPS_REQUIRE(sh, "shape is NULL");
+  IPEPS_REQUIRE(sh->Lx >= 1 && sh->Ly >= 1 && sh->d >= 1 && sh->D >= 1, "shape fields must be >= 1");
+  IPEPS_REQUIRE(sh->Lx <= 64 && sh->Ly <= 64 && sh->d <= 64 && sh->D <= 64, "shape too large");
+  ipeps::Cell c;
+  c.Lx = sh->Lx;
+  c.Ly = sh->Ly;
+  c.d = sh->d;
+  c.D = sh->D;
+  return c;
+}
+
+void check_finite(const double *p, int64_t n, cudaStream_t s, const char *what) {
+  int *cnt = static_cast<int *>(ipeps::dev_alloc(sizeof(int), s));
+  ipeps::count_nonfinite(n, p, cnt, s);
+  int h = 0;
+  cudaMemcpyAsync(&h, cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  ipeps::dev_free(cnt, s);
+  if (h) throw ipeps::Error(IPEPS_ERR_NONFINITE, std::string(what) + " contains NaN or Inf");
+}
+
+void check_env(ipeps_env env, const ipeps::Cell &c) {
+  IPEPS_REQUIRE(env, "env is NULL");
+  const auto &e = env->impl;
+  IPEPS_REQUIRE(e.cell.Lx == c.Lx && e.cell.Ly == c.Ly && e.cell.d == c.d && e.cell.D == c.D,
+                "env was built for a different shape");
+}
+
+void kron4(const double *a, const double *b, const double *c, const double *d, double *out) {
+  // out = a (x) b (x) c (x) d, all 2 x 2
+  for (int i = 0; i < 16; ++i)
+    for (int j = 0; j < 16; ++j) {
+      int i0 = (i >> 3) & 1, i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
+      int j0 = (j >> 3) & 1, j1 = (j >> 2) & 1, j2 = (j >> 1) & 1, j3 = j & 1;
+      out[i * 16 + j] = a[i0 * 2 + j0] * b[i1 * 2 + j1] * c[i2 * 2 + j2] * d[i3 * 2 + j3];
+    }
+}
+}  // namespace
+
+extern "C" {
+
+const char *ipeps_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t ipeps_launch_count(int reset) {
+  uint64_t n = ipeps::launch_counter();
+  if (reset) ipeps::launch_counter() = 0;
+  return n;
+}
+
+ipeps_status ipeps_ham_create(int d, const double *h_h, const double *h_v, const double *h_site,
+                              double scale, ipeps_ham *out) {
+  return guarded([&]() {
+    IPEPS_REQUIRE(out && h_h && h_v && d >= 1 && d <= 64, "ham_create: bad arguments");
+    auto H = std::make_unique<ipeps_ham_s>();
+    H->impl.d = d;
+    H->impl.scale = scale;
+    size_t n2 = size_t(d) * d * d * d;
+    H->impl.h.assign(h_h, h_h + n2);
+    H->impl.v.assign(h_v, h_v + n2);
+    if (h_site) {
+      H->impl.site.assign(h_site, h_site + size_t(d) * d);
+      H->impl.has_site = true;
+    }
+    for (double x : H->impl.h) IPEPS_REQUIRE(std::isfinite(x), "ham_create: non-finite h");
+    for (double x : H->impl.v) IPEPS_REQUIRE(std::isfinite(x), "ham_create: non-finite v");
+    *out = H.release();
+    return IPEPS_OK;
+  });
+}
+
+ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out) {
+  // S.S in the basis |00>,|01>,|10>,|11> (0 = up): 1/4 on the aligned states,
+  // -1/4 and the 1/2 exchange on the anti-aligned ones.  The rotated bond
+  // (second spin turned by i sigma_y: S^x -> -S^x, S^z -> -S^z) is
+  // -SxSx + SySy - SzSz.
+  double h[16] = {0};
+  if (!rotated) {
+    h[0] = 0.25; h[15] = 0.25;
+    h[5] = -0.25; h[10] = -0.25;
+    h[6] = 0.5; h[9] = 0.5;
+  } else {
+    h[0] = -0.25; h[15] = -0.25;
+    h[5] = 0.25; h[10] = 0.25;
+    h[3] = -0.5; h[12] = -0.5;
+  }
+  for (double &x : h) x *= J;
+  return ipeps_ham_create(2, h, h, nullptr, 1.0, out);
+}
+
+ipeps_status ipeps_ham_kitaev(double K, ipeps_ham *out) {
+  // tensor index s = 2 a + b; two-tensor index (a1, b1, a2, b2)
+  const double I2[4] = {1, 0, 0, 1};
+  const double Sx[4] = {0, 0.5, 0.5, 0};
+  const double Sz[4] = {0.5, 0, 0, -0.5};
+  // S^y = i Y with Y = [[0, -1/2], [1/2, 0]] real, so S^y S^y = -Y (x) Y
+  const double Y[4] = {0, -0.5, 0.5, 0};
+  double site[16], h[256], v[256];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j)
+      site[i * 4 + j] = K * Sz[(i >> 1) * 2 + (j >> 1)] * Sz[(i & 1) * 2 + (j & 1)];
+  kron4(I2, Sx, Sx, I2, h);
+  kron4(I2, Y, Y, I2, v);
+  for (int i = 0; i < 256; ++i) {
+    h[i] *= K;
+    v[i] *= -K;
+  }
+  return ipeps_ham_create(4, h, v, site, 0.5, out);
+}
+
+void ipeps_ham_destroy(ipeps_ham h) { delete h; }
+
+ipeps_status ipeps_ctmrg(const ipeps_shape *shape, const double *A_dev, int chi, double tol, int maxit,
+                         ipeps_prec prec, ipeps_env *inout_env, int *iters_out, double *err_out,
+                         ipeps_stream_t stream) {
+  return guarded([&]() {
+    ipeps::Cell c = cell_of(shape);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(A_dev && inout_env, "ctmrg: NULL argument");
+    IPEPS_REQUIRE(chi >= 1 && chi <= 4096, "ctmrg: chi out of range");
+    IPEPS_REQUIRE(maxit >= 0 && tol >= 0.0, "ctmrg: bad tol / maxit");
+    IPEPS_REQUIRE(prec == IPEPS_FP64 || prec == IPEPS_TF32X3, "ctmrg: unknown precision");
+    check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
+    std::unique_ptr<ipeps_env_s> fresh;
+    ipeps_env env = *inout_env;
+    if (!env) {
+      fresh = std::make_unique<ipeps_env_s>();
+      env = fresh.get();
+      env->impl.cell = c;
+      env->impl.chi = chi;
+      env->impl.s = s;
+      env->impl.buf = ipeps::DBuf(size_t(env->impl.total()), s);
+      ipeps::env_init(env->impl, A_dev, s);
+    } else {
+      check_env(env, c);
+      IPEPS_REQUIRE(env->impl.chi == chi, "ctmrg: env has a different chi");
+    }
+    double err = 0.0;
+    int it = 0;
+    if (maxit > 0) it = ipeps::ctmrg_run(env->impl, A_dev, tol, maxit, ipeps::Prec(prec), &err, s);
+    if (iters_out) *iters_out = it;
+    if (err_out) *err_out = err;
+    if (fresh) *inout_env = fresh.release();
+    if (maxit > 0 && !(err < tol)) {
+      g_last_error = "CTMRG reached maxit before tol";
+      return IPEPS_ERR_NOT_CONVERGED;
+    }
+    return IPEPS_OK;
+  });
+}
+
+ipeps_status ipeps_env_corner_spectra(ipeps_env env, double *out_host, size_t n, ipeps_stream_t stream) {
+  return guarded([&]() {
+    IPEPS_REQUIRE(env && out_host, "corner_spectra: NULL argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    auto &e = env->impl;
+    size_t need = size_t(4) * e.cell.nsites() * e.chi;
+    IPEPS_REQUIRE(n >= need, "corner_spectra: output too small");
+    ipeps::corner_spectra(e, s);
+    IPEPS_CUDA(cudaMemcpyAsync(out_host, e.spectra.p, need * sizeof(double), cudaMemcpyDeviceToHost, s));
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    return IPEPS_OK;
+  });
+}
+
+void ipeps_env_destroy(ipeps_env env) {
+  if (!env) return;
+  cudaStream_t s = env->impl.s;
+  delete env;
+  cudaStreamSynchronize(s);
+}
+
+ipeps_status ipeps_energy(const ipeps_shape *shape, const double *A_dev, ipeps_env env, ipeps_ham ham,
+                          double *E_out, ipeps_stream_t stream) {
+  return guarded([&]() {
+    ipeps::Cell c = cell_of(shape);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(A_dev && ham && E_out, "energy: NULL argument");
+    check_env(env, c);
+    IPEPS_REQUIRE(ham->impl.d == c.d, "energy: Hamiltonian has a different d");
+    *E_out = ipeps::energy_only(c, A_dev, env->impl, ham->impl, s);
+    if (!std::isfinite(*E_out)) throw ipeps::Error(IPEPS_ERR_NONFINITE, "energy is not finite");
+    return IPEPS_OK;
+  });
+}
+
+ipeps_status ipeps_energy_grad(const ipeps_shape *shape, const double *A_dev, ipeps_env env, ipeps_ham ham,
+                               double *E_out, double *grad_dev, ipeps_stream_t stream) {
+  return guarded([&]() {
+    ipeps::Cell c = cell_of(shape);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(A_dev && ham && E_out && grad_dev, "energy_grad: NULL argument");
+    check_env(env, c);
+    IPEPS_REQUIRE(ham->impl.d == c.d, "energy_grad: Hamiltonian has a different d");
+    check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
+    double ares = 0.0, fpres = 0.0;
+    int amv = 0;
+    *E_out = ipeps::energy_grad(c, A_dev, env->impl, ham->impl, grad_dev, s, &ares, &amv, &fpres);
+    if (!std::isfinite(*E_out)) throw ipeps::Error(IPEPS_ERR_NONFINITE, "energy is not finite");
+    if (!(ares < 1e-8)) {
+      g_last_error = "adjoint solve did not converge (relative residual " + std::to_string(ares) + ")";
+      return IPEPS_ERR_NOT_CONVERGED;
+    }
+    return IPEPS_OK;
+  });
+}
+
+ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, ipeps_env env,
+                                const double *g_dev, double delta, int krylov, int restarts,
+                                double *out_dev, double *resid_out, ipeps_stream_t stream) {
+  return guarded([&]() {
+    ipeps::Cell c = cell_of(shape);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(A_dev && g_dev && out_dev, "precondition: NULL argument");
+    IPEPS_REQUIRE(krylov >= 1 && krylov <= 1000 && restarts >= 1 && restarts <= 1000,
+                  "precondition: krylov / restarts out of range");
+    IPEPS_REQUIRE(delta >= 0.0 && std::isfinite(delta), "precondition: delta must be finite and >= 0");
+    IPEPS_REQUIRE(out_dev != g_dev, "precondition: out_dev must not alias g_dev");
+    check_env(env, c);
+    check_finite(g_dev, int64_t(c.nsites()) * c.tsize(), s, "g");
+    double r = ipeps::precondition_all(env->impl, A_dev, g_dev, delta, krylov, restarts, out_dev, s);
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    if (resid_out) *resid_out = r;
+    return IPEPS_OK;
+  });
+}
+
+void ipeps_opts_default(ipeps_opts *o) {
+  if (!o) return;
+  o->chi = 16;
+  o->ctm_tol = 1e-10;
+  o->ctm_maxit = 300;
+  o->prec = IPEPS_FP64;
+  o->precondition = 1;
+  o->krylov = 30;
+  o->restarts = 1;
+  o->delta_rule = 0;
+  o->history = 200;
+  o->maxiter = 100;
+  o->gtol = 1e-10;
+  o->E_target = -1e300;
+}
+
+ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham ham, const ipeps_opts *opts,
+                            ipeps_iter_cb cb, void *user, ipeps_stream_t stream) {
+  return guarded([&]() {
+    ipeps::Cell c = cell_of(shape);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(A_dev && ham && opts, "optimize: NULL argument");
+    IPEPS_REQUIRE(opts->chi >= 1 && opts->ctm_maxit >= 1 && opts->history >= 0 && opts->maxiter >= 0 &&
+                      opts->krylov >= 1 && opts->restarts >= 1,
+                  "optimize: bad options");
+    IPEPS_REQUIRE(ham->impl.d == c.d, "optimize: Hamiltonian has a different d");
+    check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
+    return ipeps::optimize_impl(c, A_dev, ham->impl, *opts, cb, user, s);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// Energy per site from the environment (Eq. equ:energy): nearest-neighbour
+// two-site density matrices of the 2 x 3 patches (horizontal bonds; vertical
+// bonds are the horizontal bonds of the picture rotated by 90 degrees) and
+// the single-site density matrix of the 3 x 3 patch, each normalised by its
+// own trace.  Every step is recorded on the tape so that dE/dA and dE/denv
+// come from the same pass.
+#include "common.h"
+#include "engine.h"
+#include "ipeps_impl.h"
+
+namespace ipeps {
+
+HamDev::HamDev(const HamImpl &H, cudaStream_t s)
+    : h(H.h.size(), s), v(H.v.size(), s), site(H.has_site ? H.site.size() : 0, s) {
+  IPEPS_CUDA(cudaMemcpyAsync(h.p, H.h.data(), H.h.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  IPEPS_CUDA(cudaMemcpyAsync(v.p, H.v.data(), H.v.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (H.has_site)
+    IPEPS_CUDA(cudaMemcpyAsync(site.p, H.site.data(), H.site.size() * sizeof(double),
+                               cudaMemcpyHostToDevice, s));
+}
+
+namespace {
+
+struct Patch {
+  Tape &t;
+  const Cell &c;
+  const StateVars &sv;
+  Frame f;
+  int E(int n, int x, int y) const {
+    const int Lx = f.Lx(), Ly = f.Ly();
+    x = ((x % Lx) + Lx) % Lx;
+    y = ((y % Ly) + Ly) % Ly;
+    int n0, x0, y0;
+    f.resolve(n, x, y, &n0, &x0, &y0);
+    return sv.env[n0][x0 * c.Ly + y0];
+  }
+  int A(int x, int y) const {
+    const int Lx = f.Lx(), Ly = f.Ly();
+    x = ((x % Lx) + Lx) % Lx;
+    y = ((y % Ly) + Ly) % Ly;
+    int x0, y0;
+    f.resolve_site(x, y, &x0, &y0);
+    return sv.A[f.r % 4][x0 * c.Ly + y0];
+  }
+  // left half of the patch of (x, y) with physical legs open: L[c, r, r', e, s, s']
+  int left(int x, int y) const {
+    int Lt = t_contract(t, E(C1, x, y), "ab", E(T1, x, y), "buvc", "auvc");
+    int Lb = t_contract(t, E(T3, x, y), "edfh", E(C4, x, y), "hg", "edfg");
+    int X = t_contract(t, Lt, "auvc", E(T4, x, y), "glma", "cuvlmg");
+    X = t_contract(t, X, "cuvlmg", Lb, "edfg", "cuvlmdfe");
+    X = t_contract(t, X, "cuvlmdfe", A(x, y), "suldr", "cvmfesr");
+    return t_contract(t, X, "cvmfesr", A(x, y), "tvmfw", "crwest");
+  }
+  // right half of the patch of (x, y): R[c, l, l', e, s, s']
+  int right(int x, int y) const {
+    int Rt = t_contract(t, E(T1, x, y), "cuvh", E(C2, x, y), "hi", "cuvi");
+    int Rb = t_contract(t, E(C3, x, y), "jk", E(T3, x, y), "kdfe", "jdfe");
+    int X = t_contract(t, Rt, "cuvi", E(T2, x, y), "irwj", "cuvrwj");
+    X = t_contract(t, X, "cuvrwj", Rb, "jdfe", "cuvrwdfe");
+    X = t_contract(t, X, "cuvrwdfe", A(x, y), "suldr", "cvwfesl");
+    return t_contract(t, X, "cvwfesl", A(x, y), "tvmfw", "clmest");
+  }
+};
+
+}  // namespace
+
+int energy_on_tape(Tape &t, const Cell &c, int chi, const StateVars &sv, const HamImpl &H,
+                   const HamDev &hd) {
+  (void)chi;
+  std::vector<int> terms;
+  Patch p0{t, c, sv, Frame{c.Lx, c.Ly, 0}};
+  Patch p1{t, c, sv, Frame{c.Lx, c.Ly, 1}};
+  for (int x = 0; x < c.Lx; ++x)
+    for (int y = 0; y < c.Ly; ++y) {
+      // horizontal bond (x, y)-(x+1, y)
+      int L = p0.left(x, y);
+      int R = p0.right(x + 1, y);
+      int rho = t_contract(t, L, "cxyest", R, "cxyeuv", "stuv");
+      terms.push_back(t_rho_ratio(t, rho, hd.h.p, c.d, true));
+      // on-site term from the 3 x 3 patch
+      if (H.has_site) {
+        int RC = t_contract(t, p0.E(C2, x, y), "ci", p0.E(T2, x, y), "irwj", "crwj");
+        RC = t_contract(t, RC, "crwj", p0.E(C3, x, y), "je", "crwe");
+        int r1 = t_contract(t, L, "crwest", RC, "crwe", "st");
+        terms.push_back(t_rho_ratio(t, r1, hd.site.p, c.d, false));
+      }
+      // vertical bond (x, y)-(x, y+1): in the rotated frame site (x, y) sits at
+      // (y, -x mod Lx) and its lower neighbour is its right neighbour
+      int xr = y, yr = ((-x) % c.Lx + c.Lx) % c.Lx;
+      int Lv = p1.left(xr, yr);
+      int Rv = p1.right(xr + 1, yr);
+      int rv = t_contract(t, Lv, "cxyest", Rv, "cxyeuv", "stuv");
+      terms.push_back(t_rho_ratio(t, rv, hd.v.p, c.d, true));
+    }
+  return t_sum_scalars(t, terms, H.scale / double(c.nsites()));
+}
+
+}  // namespace ipeps

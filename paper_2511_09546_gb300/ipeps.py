@@ -1,0 +1,241 @@
+"""Python binding of libipeps (argument marshalling only).
+
+Every call goes to the C ABI declared in include/ipeps.h; every step of the
+hot path runs in the library's CUDA kernels.  Device buffers are torch CUDA
+tensors (float64, contiguous) used as plain memory; the unit cell is a tensor
+of shape (Lx, Ly, d, D, D, D, D) with legs (s, u, l, d, r).  The module
+raises at import of the library if libipeps.so is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libipeps.so")
+_lib = None
+
+FP64, TF32X3 = 0, 1
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
+          5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_CANCELLED"}
+
+
+class Shape(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("d", C.c_int), ("D", C.c_int)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("chi", C.c_int), ("ctm_tol", C.c_double), ("ctm_maxit", C.c_int), ("prec", C.c_int),
+                ("precondition", C.c_int), ("krylov", C.c_int), ("restarts", C.c_int),
+                ("delta_rule", C.c_int), ("history", C.c_int), ("maxiter", C.c_int),
+                ("gtol", C.c_double), ("E_target", C.c_double)]
+
+
+class IterInfo(C.Structure):
+    _fields_ = [("iter", C.c_int), ("E", C.c_double), ("gnorm", C.c_double), ("alpha", C.c_double),
+                ("delta", C.c_double), ("evals", C.c_int), ("ctm_iters", C.c_int), ("wall_ms", C.c_double)]
+
+
+ITER_CB = C.CFUNCTYPE(C.c_int, C.POINTER(IterInfo), C.c_void_p)
+
+
+class IpepsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB_PATH):
+            raise RuntimeError(f"{_LIB_PATH} is missing; build it with __graft_entry__.build()")
+        L = C.CDLL(_LIB_PATH)
+        vp, i, d, dp = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double)
+        sp = C.POINTER(Shape)
+        L.ipeps_last_error.restype = C.c_char_p
+        L.ipeps_launch_count.restype = C.c_uint64
+        L.ipeps_launch_count.argtypes = [i]
+        L.ipeps_ham_create.argtypes = [i, dp, dp, dp, d, C.POINTER(vp)]
+        L.ipeps_ham_heisenberg.argtypes = [i, d, C.POINTER(vp)]
+        L.ipeps_ham_kitaev.argtypes = [d, C.POINTER(vp)]
+        L.ipeps_ham_destroy.argtypes = [vp]
+        L.ipeps_ctmrg.argtypes = [sp, vp, i, d, i, i, C.POINTER(vp), C.POINTER(i), dp, vp]
+        L.ipeps_env_corner_spectra.argtypes = [vp, dp, C.c_size_t, vp]
+        L.ipeps_env_destroy.argtypes = [vp]
+        L.ipeps_energy.argtypes = [sp, vp, vp, vp, dp, vp]
+        L.ipeps_energy_grad.argtypes = [sp, vp, vp, vp, dp, vp, vp]
+        L.ipeps_precondition.argtypes = [sp, vp, vp, vp, d, i, i, vp, dp, vp]
+        L.ipeps_opts_default.argtypes = [C.POINTER(Opts)]
+        L.ipeps_optimize.argtypes = [sp, vp, vp, C.POINTER(Opts), ITER_CB, vp, vp]
+        for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ctmrg",
+                     "ipeps_env_corner_spectra", "ipeps_energy", "ipeps_energy_grad",
+                     "ipeps_precondition", "ipeps_optimize"):
+            getattr(L, name).restype = i
+        _lib = L
+    return _lib
+
+
+def _check(st, allow=()):
+    if st != 0 and st not in allow:
+        raise IpepsError(st, lib().ipeps_last_error().decode())
+    return st
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(x):
+    """float64 contiguous CUDA tensor (copies host arrays to the device)."""
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64))
+    if not x.is_cuda:
+        x = x.to("cuda")
+    if x.dtype != torch.float64:
+        raise TypeError("float64 tensors expected")
+    return x.contiguous()
+
+
+def _shape(A):
+    Lx, Ly, d, D = A.shape[0], A.shape[1], A.shape[2], A.shape[3]
+    return Shape(Lx, Ly, d, D)
+
+
+def cell_tensor(cell):
+    """Stack a nested list cell[x][y] of (d, D, D, D, D) arrays into (Lx, Ly, d, D, D, D, D)."""
+    return np.stack([np.stack([np.asarray(a, dtype=np.float64) for a in col]) for col in cell])
+
+
+class Ham:
+    def __init__(self, handle):
+        self.h = handle
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipeps_ham_destroy(self.h)
+            self.h = None
+
+
+def ham_create(d, h, v, site=None, scale=1.0):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    dp = C.POINTER(C.c_double)
+    sp = None if site is None else np.ascontiguousarray(site, dtype=np.float64)
+    out = C.c_void_p()
+    _check(lib().ipeps_ham_create(d, h.ctypes.data_as(dp), v.ctypes.data_as(dp),
+                                  None if sp is None else sp.ctypes.data_as(dp), scale, C.byref(out)))
+    return Ham(out)
+
+
+def ham_heisenberg(rotated=True, J=1.0):
+    out = C.c_void_p()
+    _check(lib().ipeps_ham_heisenberg(int(rotated), J, C.byref(out)))
+    return Ham(out)
+
+
+def ham_kitaev(K=-1.0):
+    out = C.c_void_p()
+    _check(lib().ipeps_ham_kitaev(K, C.byref(out)))
+    return Ham(out)
+
+
+class Env:
+    def __init__(self, handle, shape, chi):
+        self.h, self.shape, self.chi = handle, shape, chi
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ipeps_env_destroy(self.h)
+            self.h = None
+
+    def corner_spectra(self):
+        n = 4 * self.shape.Lx * self.shape.Ly * self.chi
+        out = np.zeros(n)
+        _check(lib().ipeps_env_corner_spectra(self.h, out.ctypes.data_as(C.POINTER(C.c_double)), n, _stream()))
+        return out.reshape(4, self.shape.Lx * self.shape.Ly, self.chi)
+
+
+def ctmrg(A, chi, tol=1e-10, maxit=500, prec=FP64, env=None, allow_unconverged=False):
+    """CTMRG environment of the cell A.  Returns (env, iterations, final change)."""
+    A = _dev(A)
+    shape = _shape(A)
+    h = C.c_void_p(env.h if env is not None else None)
+    it = C.c_int()
+    err = C.c_double()
+    st = lib().ipeps_ctmrg(C.byref(shape), C.c_void_p(A.data_ptr()), chi, tol, maxit, prec, C.byref(h),
+                           C.byref(it), C.byref(err), _stream())
+    if env is None and h.value:
+        env = Env(h, shape, chi)
+    _check(st, allow=(5,) if allow_unconverged else ())
+    return env, it.value, err.value
+
+
+def energy(A, env, ham):
+    A = _dev(A)
+    shape = _shape(A)
+    E = C.c_double()
+    _check(lib().ipeps_energy(C.byref(shape), C.c_void_p(A.data_ptr()), env.h, ham.h, C.byref(E), _stream()))
+    return E.value
+
+
+def energy_grad(A, env, ham):
+    """(E, dE/dA) at the CTMRG fixed point; dE/dA has the shape of A."""
+    A = _dev(A)
+    shape = _shape(A)
+    g = torch.empty_like(A)
+    E = C.c_double()
+    _check(lib().ipeps_energy_grad(C.byref(shape), C.c_void_p(A.data_ptr()), env.h, ham.h, C.byref(E),
+                                   C.c_void_p(g.data_ptr()), _stream()))
+    return E.value, g
+
+
+def precondition(A, env, g, delta, krylov=30, restarts=1):
+    """P^-1 g with P = 1 (x) M + delta I per tensor.  Returns (x, worst relative residual)."""
+    A = _dev(A)
+    g = _dev(g)
+    shape = _shape(A)
+    out = torch.empty_like(g)
+    res = C.c_double()
+    _check(lib().ipeps_precondition(C.byref(shape), C.c_void_p(A.data_ptr()), env.h, C.c_void_p(g.data_ptr()),
+                                    delta, krylov, restarts, C.c_void_p(out.data_ptr()), C.byref(res), _stream()))
+    return out, res.value
+
+
+def default_opts(**kw):
+    o = Opts()
+    lib().ipeps_opts_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def optimize(A, ham, opts, callback=None):
+    """Run L-BFGS in place on a device copy of A.  Returns (A_final, log, status)."""
+    A = _dev(A).clone()
+    shape = _shape(A)
+    log = []
+
+    def _cb(info_p, _user):
+        i = info_p.contents
+        rec = dict(iter=i.iter, E=i.E, gnorm=i.gnorm, alpha=i.alpha, delta=i.delta, evals=i.evals,
+                   ctm_iters=i.ctm_iters, wall_ms=i.wall_ms)
+        log.append(rec)
+        if callback is not None and callback(rec):
+            return 1
+        return 0
+
+    cb = ITER_CB(_cb)
+    st = lib().ipeps_optimize(C.byref(shape), C.c_void_p(A.data_ptr()), ham.h, C.byref(opts), cb, None, _stream())
+    _check(st, allow=(5, 7))
+    return A, log, st
+
+
+def launch_count(reset=False):
+    return int(lib().ipeps_launch_count(1 if reset else 0))
