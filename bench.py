@@ -1,0 +1,312 @@
+"""Benchmark of the GB300 preconditioned iPEPS hot path.
+
+One step is one preconditioned L-BFGS iteration of the workload (CTMRG run to
+its fixed point warm-started from the previous point, energy, fixed-point
+gradient, local-metric preconditioner P^-1 g by GMRES(30), the Hager-Zhang
+line search).  The default workload is the square-lattice Heisenberg model on
+a 1x1 cell with d=2, D=4, chi=64, started from the seeded Neel-like D=1 state
+embedded in D=4 plus noise.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--prec fp64|tf32x3] [--workload NAME]
+
+--impl reference times the CPU FP64 oracle on a bounded sample of the same
+workload (the oracle is the only reference this method has).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("preconditioned L-BFGS iterations/s (Heisenberg 1x1 iPEPS, CTMRG fixed point + energy + "
+          "fixed-point gradient + local-metric GMRES(30) preconditioner per iteration)")
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x ~2.07 GHz)
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}",
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(smax)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import inputs, ipeps
+
+    torch.cuda.set_device(local)
+    w = inputs.WORKLOADS[args.workload]
+    cell = w["gen"]()
+    A_host = ipeps.cell_tensor(cell)
+    ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+    prec = ipeps.TF32X3 if args.prec == "tf32x3" else ipeps.FP64
+    K, W = args.steps, args.warmup
+    opts = ipeps.default_opts(chi=w["chi"], maxiter=W + K, precondition=1, ctm_tol=1e-10, ctm_maxit=300,
+                              prec=prec, gtol=0.0)
+    A = torch.as_tensor(A_host, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    starts, ends = {}, {}
+    state = {"launch0": 0, "clocks": None}
+
+    def cb(rec):
+        i = rec["iter"]
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        ends[i] = ev
+        if i == W:
+            torch.cuda.synchronize()
+            if world > 1:
+                torch.distributed.barrier()
+            ipeps.profile(True)
+            state["launch0"] = ipeps.launch_count()
+            state["clocks"] = Clocks(local)
+        if i >= W + K:
+            return 0
+        flush.fill_(float(i))  # L2 flush between iterations, outside the timed spans
+        st = torch.cuda.Event(enable_timing=True)
+        st.record(stream)
+        starts[i + 1] = st
+        return 0
+
+    torch.cuda.synchronize()
+    Af, log, status = ipeps.optimize(A, ham, opts, callback=cb)
+    torch.cuda.synchronize()
+    launches = ipeps.launch_count() - state["launch0"]
+    prof = ipeps.profile_stats()
+    ipeps.profile(False)
+    clocks = state["clocks"].stop() if state["clocks"] else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+    timed = [i for i in range(W + 1, W + K + 1) if i in starts and i in ends]
+    lat = [starts[i].elapsed_time(ends[i]) for i in timed]
+    total_ms = sum(lat)
+    t_local = np.array([total_ms], dtype=np.float64)
+    if world > 1:
+        tt = torch.tensor(t_local, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_local = tt.cpu().numpy()
+    total_ms = float(t_local[0])
+    n_timed = len(timed)
+    value = world * n_timed / (total_ms / 1000.0) if total_ms > 0 else 0.0
+
+    # ---- end to end through the C ABI with host buffers (H2D + D2H inside)
+    torch.cuda.synchronize()
+    host = torch.as_tensor(A_host).pin_memory()
+    out_host = torch.empty_like(host).pin_memory()
+    opts_e2e = ipeps.default_opts(chi=w["chi"], maxiter=K, precondition=1, ctm_tol=1e-10, ctm_maxit=300,
+                                  prec=prec, gtol=0.0)
+    t0 = time.perf_counter()
+    Ad = host.to("cuda", non_blocking=True)
+    Ae, log_e2e, _ = ipeps.optimize(Ad, ham, opts_e2e)
+    out_host.copy_(Ae, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_iters = max(1, len(log_e2e) - 1)
+
+    # ---- roofline of the dominant kernel class (live CUDA events)
+    roof = None
+    if prof:
+        dom = max(prof, key=lambda k: prof[k]["ms"])
+        st = prof[dom]
+        if dom == "tc_gemm":
+            peaks = _peaks()
+            peak = peaks.get("bf16_tflops_sustained", 1703.6) / 2.0
+            roof = {"kernel": dom, "bound": "tensor", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
+                    "peak": peak, "unit": "TFLOP/s", "peak_source": "measured bf16 sustained x 1/2 (tf32 ratio)"}
+        elif st["flops"] > 0:
+            roof = {"kernel": dom, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "peak_source": "nominal FP64 (152 SM x 2 DFMA/clk x 2 x 2.07 GHz)"}
+        else:
+            peaks = _peaks()
+            roof = {"kernel": dom, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
+                    "peak": peaks.get("hbm_gbs", 6750.4), "unit": "GB/s", "peak_source": "measured hbm_gbs"}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["traffic"] = None
+        roof["share"] = st["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))
+        roof["launches"] = st["count"]
+    ctm_flops = sum(v["flops"] for k, v in prof.items() if k in ("dgemm", "tc_gemm"))
+    rec = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "iter/s",
+        "n_gpus": world,
+        "steps": n_timed,
+        "warmup": W,
+        "ms_per_step": total_ms / max(1, n_timed),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == ipeps.FP64 else "tf32x3+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload + ": Heisenberg square lattice 1x1, d=2, D=4, chi=64, "
+                   "Neel-like D=1 seed in D=4 + 1e-2 noise (seed 0)" if args.workload == "heis_d4_chi64"
+                   else args.workload,
+                   "precision": args.prec, "l2": "flushed (256 MB write) between timed iterations",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "chi": w["chi"], "D": w["D"]},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat else None,
+                       "p99": float(np.percentile(lat, 99)) if lat else None},
+        "gemm_tflops": ctm_flops / (total_ms * 1e-3) / 1e12 if total_ms > 0 else None,
+        "energy": log[-1]["E"] if log else None,
+        "status": status,
+        "roofline": roof,
+        "e2e": {"value": e2e_iters / e2e_s, "unit": "iter/s",
+                "h2d_bytes_per_step": int(host.numel() * 8 / e2e_iters),
+                "d2h_bytes_per_step": int(host.numel() * 8 / e2e_iters)},
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3)} for k, v in prof.items()},
+    }
+    return rec, log
+
+
+def oracle_sample(workload, n_ctm=1):
+    """Oracle time of n_ctm CTMRG iterations at the workload size (seconds each)."""
+    import torch
+
+    from oracle import ctmrg as OC
+    from paper_2511_09546_gb300 import inputs
+
+    w = inputs.WORKLOADS[workload]
+    cell = w["gen"]()
+    Lx, Ly = w["Lx"], w["Ly"]
+    A = OC.as_torch_cell(cell)
+    with torch.no_grad():
+        env = OC.init_env(Lx, Ly, A)
+        env = OC.ctmrg_step(Lx, Ly, A, env, w["chi"])  # grow chi to its working size
+        t0 = time.perf_counter()
+        for _ in range(n_ctm):
+            env = OC.ctmrg_step(Lx, Ly, A, env, w["chi"])
+        dt = (time.perf_counter() - t0) / n_ctm
+    return dt, torch.get_num_threads()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3"])
+    ap.add_argument("--workload", default="heis_d4_chi64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = _dist()
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the oracle: each step is one CTMRG iteration of the workload, scaled to
+        # L-BFGS iterations by a CTMRG-iterations-per-step count of 10 (the
+        # warm-started evaluations of one step); gradient and preconditioner are
+        # not included, so this is an upper bound on the oracle's rate
+        per_step_ctm = 10
+        times = []
+        for _ in range(args.warmup + args.steps):
+            dt, cores = oracle_sample(args.workload, 1)
+            times.append(dt)
+        t = statistics.mean(times[args.warmup:]) * per_step_ctm
+        v = 1.0 / t
+        rec = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+               "config": {"workload": args.workload, "precision": "fp64"},
+               "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                                "sample": f"1 oracle CTMRG iteration per step x {per_step_ctm} CTMRG "
+                                          "iterations per L-BFGS step; gradient/preconditioner excluded"},
+               "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(rec), flush=True)
+        return
+    import torch
+
+    if world > 1:
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    rec, log = run_ours(args, rank, world, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            # measured after the GPU run: ctm iterations per step from the run's log
+            steps = [r for r in log[args.warmup + 1:]] or log[1:]
+            ctm_per_step = statistics.mean([max(1, r["ctm_iters"]) * max(1, r["evals"]) for r in steps]) if steps else 10
+            dt, cores = oracle_sample(args.workload, 1)
+            v = 1.0 / (dt * ctm_per_step)
+            rec["cpu_baseline"] = {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+                                   "sample": f"1 oracle CTMRG iteration ({dt:.2f} s) x {ctm_per_step:.1f} CTMRG "
+                                             "iterations per L-BFGS step of the GPU run; gradient and "
+                                             "preconditioner excluded (upper bound on the oracle's rate)"}
+        print(json.dumps(rec), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -163,10 +163,30 @@ ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham h
                             const ipeps_opts *opts, ipeps_iter_cb cb, void *user,
                             ipeps_stream_t stream);
 
+/* ------------------------------------------------------------- GEMM */
+/* The contraction engine's GEMM (row-major): C = alpha op(A) op(B) + beta C,
+ * op(A) M x K (ta != 0: A stored K x M), op(B) K x N (tb != 0: B stored
+ * N x K), device pointers, leading dimensions in elements.  prec selects the
+ * FP64 CUDA-core kernels or the 3xTF32 tcgen05 kernel (FP32 accumulate).
+ * Every contraction of the hot path lowers to this call (after at most one
+ * permutation per operand). */
+ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                        double *C, int64_t ldc, ipeps_stream_t stream);
+
 /* ------------------------------------------------------------- misc */
 const char *ipeps_last_error(void);
 /* Kernel launches issued by this thread since the last reset (for reports). */
 uint64_t ipeps_launch_count(int reset);
+/* Live kernel timing: enable != 0 clears the statistics and records a CUDA
+ * event pair around every instrumented launch on its stream; 0 stops.
+ * ipeps_profile_query fills the launch count, summed duration (ms) and the
+ * algorithmic FLOPs and bytes of one kernel class ("dgemm", "tc_gemm",
+ * "jacobi_pair", "permute"); returns 0 if that class never ran.
+ * ipeps_profile_names lists the classes seen (comma separated). */
+void ipeps_profile(int enable);
+int ipeps_profile_query(const char *name, uint64_t *count, double *ms, double *flops, double *bytes);
+const char *ipeps_profile_names(void);
 
 #ifdef __cplusplus
 }

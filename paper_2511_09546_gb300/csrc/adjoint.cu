@@ -9,7 +9,10 @@
 // hand-written adjoints of the F tape with a new cotangent.
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "common.h"
@@ -36,9 +39,20 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   const int ns = c.nsites();
   const int64_t nenv = e.total(), ta = c.tsize();
   HamDev hd(H, s);
+  const bool dbg = std::getenv("IPEPS_DEBUG") != nullptr;
+  auto t0 = std::chrono::steady_clock::now();
+  auto lap = [&](const char *what) {
+    if (!dbg) return;
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    auto t1 = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[ipeps] energy_grad %s: %.1f ms\n", what,
+                 std::chrono::duration<double, std::milli>(t1 - t0).count());
+    t0 = t1;
+  };
 
   // ---- F tape at e*
   Tape tF(s);
+  tF.vcache = &e.svd_cache;
   StateVars in = state_leaves(tF, e, A_dev);
   StateVars out = in;
   ctmrg_iteration(tF, c, e.chi, out);
@@ -54,6 +68,7 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
       outs[k] = t_signs(tF, out.env[n][i], sig.p + int64_t(2 * k) * e.chi, sig.p + int64_t(2 * k + 1) * e.chi);
     }
   if (fp_resid) *fp_resid = fpres;
+  lap("F tape + sign gauge");
 
   // ---- energy tape: E, dE/de, dE/dA
   Tape tE(s);
@@ -78,6 +93,15 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
     if (g) axpy(ta, 1.0, g, grad + int64_t(i) * ta, s);
   }
   tE.clear();
+  lap("energy tape");
+  if (dbg) {
+    DBuf nb(1, s);
+    nrm2(nenv, ebar.p, nb.p, s);
+    double h;
+    IPEPS_CUDA(cudaMemcpyAsync(&h, nb.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    std::fprintf(stderr, "[ipeps] |dE/denv| = %.6e\n", h);
+  }
 
   // ---- vector-Jacobian products of F
   auto vjp = [&](const double *lam, double *out_env, double *out_A) {
@@ -112,7 +136,14 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   };
   DBuf lam(size_t(nenv), s);
   int nmv = 0;
-  double rel = gmres_dev(nenv, mv, ebar.p, lam.p, 40, 12, 1e-12, s, &nmv);
+  int kry = 40, rst = 6;
+  if (const char *v = std::getenv("IPEPS_ADJ_KRYLOV")) kry = std::atoi(v);
+  if (const char *v = std::getenv("IPEPS_ADJ_RESTARTS")) rst = std::atoi(v);
+  double rel = gmres_dev(nenv, mv, ebar.p, lam.p, kry, rst, 1e-12, s, &nmv);
+  lap("adjoint GMRES");
+  if (dbg)
+    std::fprintf(stderr, "[ipeps] adjoint: %d matvecs, residual %.2e, fixed-point residual %.2e, cg %d\n", nmv,
+                 rel, fpres, tF.svd_iters);
   vjp(lam.p, nullptr, grad);
   IPEPS_CUDA(cudaStreamSynchronize(s));
   if (adj_resid) *adj_resid = rel;

@@ -11,6 +11,8 @@
 #include "common.h"
 #include "ipeps_impl.h"
 #include "kernels.h"
+#include "profile.h"
+#include "engine.h"
 
 struct ipeps_env_s {
   ipeps::EnvImpl impl;
@@ -121,6 +123,19 @@ void kron4(const double *a, const double *b, const double *c, const double *d, d
 extern "C" {
 
 const char *ipeps_last_error(void) { return g_last_error.c_str(); }
+
+void ipeps_profile(int enable) { ipeps::profile_enable(enable != 0); }
+
+int ipeps_profile_query(const char *name, uint64_t *count, double *ms, double *flops, double *bytes) {
+  if (!name || !count || !ms || !flops || !bytes) return 0;
+  return ipeps::profile_query(name, count, ms, flops, bytes) ? 1 : 0;
+}
+
+const char *ipeps_profile_names(void) {
+  static thread_local std::string names;
+  names = ipeps::profile_names();
+  return names.c_str();
+}
 
 uint64_t ipeps_launch_count(int reset) {
   uint64_t n = ipeps::launch_counter();
@@ -301,6 +316,22 @@ ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, i
     double r = ipeps::precondition_all(env->impl, A_dev, g_dev, delta, krylov, restarts, out_dev, s);
     IPEPS_CUDA(cudaStreamSynchronize(s));
     if (resid_out) *resid_out = r;
+    return IPEPS_OK;
+  });
+}
+
+ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                        const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                        int64_t ldc, ipeps_stream_t stream) {
+  return guarded([&]() {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(M >= 0 && N >= 0 && K >= 0, "gemm: negative size");
+    IPEPS_REQUIRE(A && B && C, "gemm: NULL pointer");
+    IPEPS_REQUIRE(lda >= (ta ? M : K) && ldb >= (tb ? K : N) && ldc >= N, "gemm: leading dimension too small");
+    if (prec == IPEPS_TF32X3) ipeps::gemm_tf32x3(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    else if (prec == IPEPS_FP64) ipeps::gemm_f64(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    else throw ipeps::Error(IPEPS_ERR_ARG, "gemm: unknown precision");
+    IPEPS_CUDA(cudaStreamSynchronize(s));
     return IPEPS_OK;
   });
 }

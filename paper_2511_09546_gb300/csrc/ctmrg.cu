@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <queue>
 #include <tuple>
@@ -153,6 +155,7 @@ void left_move(Tape &t, const Cell &c, int chi, StateVars &sv, int r) {
       int M = t_contract(t, R2, "ab", R1, "bc", "ac");
       int N = int(t.val(M).d[0]);
       int U, S, V;
+      t.vkey = (r * 64 + x) * 64 + y;
       t_svd(t, M, std::min(chi, N), &U, &S, &V);
       int fs = t_inv_sqrt_cut(t, S, kSvCutoff);
       Pup[x * Ly + y] = t_scale_cols(t, t_contract(t, R2, "ba", U, "bk", "ak"), fs);
@@ -230,7 +233,8 @@ __global__ void spectra_kernel(const double *G, int chi, double *out) {
     double nrm = 0.0;
     for (int i = 0; i < chi; ++i) nrm += sv[i] * sv[i];
     nrm = sqrt(nrm);
-    for (int i = 0; i < chi; ++i) sv[i] = nrm > 0 ? sv[i] / nrm : 0.0;
+    // non-finite input must not look converged: propagate it
+    for (int i = 0; i < chi; ++i) sv[i] = (nrm > 0 || !isfinite(nrm)) ? sv[i] / nrm : 0.0;
   }
   __syncthreads();
   for (int j = threadIdx.x; j < chi; j += blockDim.x) out[int64_t(blockIdx.x) * chi + j] = sv[j];
@@ -292,8 +296,24 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
       Tape t(s);
       t.record = false;
       t.prec = prec;
+      t.vcache = &e.svd_cache;
       StateVars sv = state_leaves(t, e, A_dev);
       ctmrg_iteration(t, c, e.chi, sv);
+      // align the sign gauge of every chi bond with the previous iteration, so
+      // that the environment (and the warm starts of the projector SVDs)
+      // converge elementwise
+      std::vector<const double *> cand(8 * c.nsites());
+      for (int n = 0; n < 8; ++n)
+        for (int i = 0; i < c.nsites(); ++i) cand[n * c.nsites() + i] = t.vp(sv.env[n][i]);
+      double res = 0.0;
+      DBuf sig = solve_signs(e, cand, s, &res);
+      const int64_t D2 = int64_t(c.D) * c.D;
+      for (int n = 0; n < 8; ++n)
+        for (int i = 0; i < c.nsites(); ++i) {
+          int k = n * c.nsites() + i;
+          leg_signs(t.vp(sv.env[n][i]), e.chi, n < 4 ? 1 : D2, e.chi, sig.p + int64_t(2 * k) * e.chi,
+                    sig.p + int64_t(2 * k + 1) * e.chi, s);
+        }
       // new tensors into a staging buffer, then over the old ones
       DBuf nb(size_t(e.total()), s);
       for (int n = 0; n < 8; ++n)
@@ -304,6 +324,27 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
                                      cudaMemcpyDeviceToDevice, s));
         }
       std::swap(e.buf, nb);
+      {
+        int *cnt = static_cast<int *>(dev_alloc(sizeof(int), s));
+        int bad = 0;
+        count_nonfinite(e.total(), e.buf.p, cnt, s);
+        IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IPEPS_CUDA(cudaStreamSynchronize(s));
+        dev_free(cnt, s);
+        if (bad) throw Error(IPEPS_ERR_NONFINITE, "CTMRG produced non-finite environment tensors");
+      }
+      if (std::getenv("IPEPS_DEBUG_NAN")) {
+        int *cnt = static_cast<int *>(dev_alloc(sizeof(int), s));
+        for (int n = 0; n < 8; ++n)
+          for (int i = 0; i < c.nsites(); ++i) {
+            int x = i / c.Ly, y = i % c.Ly, bad = 0;
+            count_nonfinite(n < 4 ? e.csize() : e.esize(), e.ptr(n, x, y), cnt, s);
+            IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+            IPEPS_CUDA(cudaStreamSynchronize(s));
+            if (bad) std::fprintf(stderr, "[ipeps] ctmrg it %d: tensor %d site %d has %d non-finite entries\n", it, n, i, bad);
+          }
+        dev_free(cnt, s);
+      }
     }
     corner_spectra(e, s);
     change = spectra_change(prev.p, e.spectra.p, nmat, e.chi, s);

@@ -5,6 +5,10 @@
 #include <cmath>
 #include <map>
 #include <numeric>
+#include <chrono>
+#include <cstdio>
+#include <typeinfo>
+#include <cstdlib>
 
 #include "common.h"
 #include "engine.h"
@@ -120,7 +124,30 @@ void Tape::zero_grads() {
 }
 
 void Tape::backward() {
-  for (auto it = nodes.rbegin(); it != nodes.rend(); ++it) (*it)->backward(*this);
+  static const bool dbg = std::getenv("IPEPS_DEBUG_NAN") != nullptr;
+  int idx = int(nodes.size());
+  for (auto it = nodes.rbegin(); it != nodes.rend(); ++it) {
+    --idx;
+    auto t0 = std::chrono::steady_clock::now();
+    (*it)->backward(*this);
+    if (dbg) {
+      // report the first node whose adjoint produced a non-finite cotangent
+      int *cnt = static_cast<int *>(dev_alloc(sizeof(int), s));
+      int bad = 0;
+      for (size_t v = 0; v < vars.size() && !bad; ++v) {
+        if (!vars[v].grad.p) continue;
+        count_nonfinite(vars[v].val.size(), vars[v].grad.p, cnt, s);
+        IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IPEPS_CUDA(cudaStreamSynchronize(s));
+        if (bad) std::fprintf(stderr, "[ipeps] non-finite cotangent after node %d (%s), var %zu\n", idx,
+                              typeid(**it).name(), v);
+      }
+      dev_free(cnt, s);
+      double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (ms > 50.0) std::fprintf(stderr, "[ipeps] node %d (%s) backward %.1f ms\n", idx, typeid(**it).name(), ms);
+      if (bad) throw Error(IPEPS_ERR_NONFINITE, "non-finite cotangent in the adjoint");
+    }
+  }
 }
 
 void Tape::clear() {
@@ -345,6 +372,16 @@ struct RhoRatioNode : Node {
   void backward(Tape &t) override {
     double *go = t.grad(out, false);
     if (!go) return;
+    if (std::getenv("IPEPS_DEBUG_NAN")) {
+      double hv[4];
+      IPEPS_CUDA(cudaMemcpyAsync(hv, num.p, 8, cudaMemcpyDeviceToHost, t.s));
+      IPEPS_CUDA(cudaMemcpyAsync(hv + 1, den.p, 8, cudaMemcpyDeviceToHost, t.s));
+      IPEPS_CUDA(cudaMemcpyAsync(hv + 2, t.vp(out), 8, cudaMemcpyDeviceToHost, t.s));
+      IPEPS_CUDA(cudaMemcpyAsync(hv + 3, go, 8, cudaMemcpyDeviceToHost, t.s));
+      IPEPS_CUDA(cudaStreamSynchronize(t.s));
+      std::fprintf(stderr, "[ipeps] rho_ratio num %.6e den %.6e out %.6e gout %.6e d %d two %d\n", hv[0], hv[1],
+                   hv[2], hv[3], d, int(two));
+    }
     rho_ratio_bwd<<<1, 256, 0, t.s>>>(h, d, two ? 1 : 0, den.p, t.vp(out), go, t.grad(rho));
     count_launch();
     check_launch("rho_ratio_bwd");
@@ -568,6 +605,47 @@ void t_svd(Tape &t, int M, int k, int *U, int *S, int *V) {
   IPEPS_REQUIRE(d.size() == 2 && d[0] == d[1], "t_svd: square matrix expected");
   int64_t N = d[0];
   IPEPS_REQUIRE(k >= 1 && k <= N, "t_svd: bad rank");
+  int64_t kb = std::min<int64_t>(N, ((k + std::max(16, k / 4)) + 1) / 2 * 2);
+  if (kb % 2) --kb;
+  if (t.vcache && kb >= k && kb < N && N > 256) {
+    // truncated SVD: warm-started subspace iteration over a kb-block; a cold
+    // start (or a rank-deficient block) takes the full Jacobi SVD once and
+    // seeds the warm start from it
+    DBuf &vc = (*t.vcache)[t.vkey];
+    const size_t csz = size_t(N * kb + kb);
+    bool warm = vc.p != nullptr && vc.n == csz;
+    DBuf Ub(size_t(N * kb), t.s), Sb(size_t(kb), t.s), Vb(size_t(N * kb), t.s);
+    int its = 0;
+    bool ok = warm && svd_subspace(t.vp(M), N, k, int(kb), vc.p, Ub.p, Sb.p, Vb.p, t.s, &its);
+    t.svd_iters += its;
+    if (!ok) {
+      if (std::getenv("IPEPS_DEBUG"))
+        std::fprintf(stderr, "[ipeps] t_svd key %d N %lld: full SVD (%s)\n", t.vkey, (long long)N,
+                     warm ? "block failed" : "cold");
+      DBuf Uf(size_t(N * N), t.s), Sf(size_t(N), t.s), Vf(size_t(N * N), t.s);
+      svd_full(t.vp(M), N, Uf.p, Sf.p, Vf.p, t.s);
+      copy_cols_kernel<<<256, 256, 0, t.s>>>(Uf.p, N, N, kb, Ub.p);
+      copy_cols_kernel<<<256, 256, 0, t.s>>>(Vf.p, N, N, kb, Vb.p);
+      count_launch(2);
+      IPEPS_CUDA(cudaMemcpyAsync(Sb.p, Sf.p, kb * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
+      if (!warm) vc = DBuf(csz, t.s);
+      IPEPS_CUDA(cudaMemcpyAsync(vc.p, Vb.p, N * kb * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
+      IPEPS_CUDA(cudaMemcpyAsync(vc.p + N * kb, Sb.p, kb * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
+      IPEPS_CUDA(cudaStreamSynchronize(t.s));
+    }
+    svd_sign_kernel<<<unsigned(k), 256, 0, t.s>>>(Ub.p, Vb.p, N, kb);
+    *U = t.make({N, int64_t(k)});
+    *V = t.make({N, int64_t(k)});
+    *S = t.make({int64_t(k)});
+    copy_cols_kernel<<<256, 256, 0, t.s>>>(Ub.p, N, kb, k, t.vp(*U));
+    copy_cols_kernel<<<256, 256, 0, t.s>>>(Vb.p, N, kb, k, t.vp(*V));
+    count_launch(3);
+    check_launch("t_svd block");
+    IPEPS_CUDA(cudaMemcpyAsync(t.vp(*S), Sb.p, k * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
+    if (t.record) push_trunc_svd_node(t, M, *U, *S, *V, N, k, int(kb), std::move(Ub), std::move(Sb), std::move(Vb));
+    else IPEPS_CUDA(cudaStreamSynchronize(t.s));
+    return;
+  }
   auto *nd = new SVDNode;
   nd->N = N; nd->k = k; nd->M = M;
   nd->Uf = DBuf(size_t(N * N), t.s);

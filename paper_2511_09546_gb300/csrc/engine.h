@@ -11,6 +11,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <map>
 #include <memory>
 #include <string>
 #include <vector>
@@ -60,6 +61,11 @@ struct Tape {
   bool record = true;
   std::vector<Var> vars;
   std::vector<std::unique_ptr<Node>> nodes;
+  // warm-start blocks of the truncated SVD, keyed per projector cut (forward
+  // passes that are not recorded use subspace iteration from these)
+  std::map<int, DBuf> *vcache = nullptr;
+  int vkey = 0;
+  int svd_iters = 0;  // subspace iterations spent (statistics)
 
   explicit Tape(cudaStream_t st) : s(st) {}
   int leaf(double *p, const std::vector<int64_t> &d);   // external memory, not owned
@@ -100,5 +106,14 @@ int t_sum_scalars(Tape &t, const std::vector<int> &xs, double scale);
 
 // full SVD of a row-major N x N matrix: U, V row-major N x N, S descending
 void svd_full(const double *M, int64_t N, double *U, double *S, double *V, cudaStream_t s);
+// top-k singular triplets (k even, chi <= k <= N) by subspace iteration warm
+// started from cache = [V (N x k) | S (k)], which receives the new block.
+// U, V row-major N x k, S descending.  Returns false (nothing written to the
+// cache) when the block is numerically rank deficient; callers then use svd_full.
+bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, double *U, double *S,
+                  double *V, cudaStream_t s, int *iters);
+// records the adjoint of the top-chi triplets computed from a kb-block
+void push_trunc_svd_node(Tape &t, int M, int U, int S, int V, int64_t N, int chi, int kb, DBuf &&Uk,
+                         DBuf &&Sk, DBuf &&Vk);
 
 }  // namespace ipeps

@@ -3,8 +3,11 @@
 // shape the CTMRG produces; the kernel favours simplicity and exact FP64.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "common.h"
 #include "kernels.h"
+#include "profile.h"
 
 namespace ipeps {
 
@@ -15,23 +18,33 @@ __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M,
                                                     double alpha, const double *__restrict__ A,
                                                     int64_t lda, const double *__restrict__ B,
                                                     int64_t ldb, double beta, double *__restrict__ C,
-                                                    int64_t ldc, int64_t sA, int64_t sB, int64_t sC) {
+                                                    int64_t ldc, int64_t sA, int64_t sB, int64_t sC,
+                                                    int64_t kchunk) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
+  // batched: blockIdx.z selects the matrix; split-K (kchunk > 0): blockIdx.z
+  // selects a K range and C is the slice's partial-sum buffer
   const int64_t bz = blockIdx.z;
-  A += bz * sA;
-  B += bz * sB;
-  C += bz * sC;
+  int64_t kbeg = 0, kend = K;
+  if (kchunk > 0) {
+    kbeg = bz * kchunk;
+    kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+    C += bz * sC;
+  } else {
+    A += bz * sA;
+    B += bz * sB;
+    C += bz * sC;
+  }
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
   double acc[4][4] = {};
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
     for (int e = threadIdx.x; e < BM * BK; e += 256) {
       int mm, kk;
       if (!ta) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
       int64_t gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
-      if (gm < M && gk < K) v = ta ? A[gk * lda + gm] : A[gm * lda + gk];
+      if (gm < M && gk < kend) v = ta ? A[gk * lda + gm] : A[gm * lda + gk];
       As[kk][mm] = v;
     }
     for (int e = threadIdx.x; e < BN * BK; e += 256) {
@@ -39,7 +52,7 @@ __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M,
       if (!tb) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
       int64_t gn = n0 + nn, gk = k0 + kk;
       double v = 0.0;
-      if (gn < N && gk < K) v = tb ? B[gn * ldb + gk] : B[gk * ldb + gn];
+      if (gn < N && gk < kend) v = tb ? B[gn * ldb + gk] : B[gk * ldb + gn];
       Bs[kk][nn] = v;
     }
     __syncthreads();
@@ -71,6 +84,69 @@ __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M,
     }
   }
 }
+// Small output (M N <= 1024), long K: block z takes a K slice, each warp a set
+// of outputs, lanes stride over k; partial sums go to W[z] (reduced below).
+__global__ void __launch_bounds__(256) multidot_kernel(bool ta, bool tb, int64_t M, int64_t N, int64_t K,
+                                                       double alpha, const double *__restrict__ A, int64_t lda,
+                                                       const double *__restrict__ B, int64_t ldb,
+                                                       double *__restrict__ W, int64_t kchunk) {
+  const int64_t z = blockIdx.x;
+  const int64_t kbeg = z * kchunk, kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t o = warp; o < M * N; o += 8) {
+    const int64_t m = o / N, n = o % N;
+    double acc = 0.0;
+    for (int64_t k = kbeg + lane; k < kend; k += 32) {
+      double a = ta ? A[k * lda + m] : A[m * lda + k];
+      double b = tb ? B[n * ldb + k] : B[k * ldb + n];
+      acc = fma(a, b, acc);
+    }
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) W[z * M * N + o] = alpha * acc;
+  }
+}
+
+// One thread per output element (one of M, N small, K moderate): no tile waste.
+__global__ void perout_kernel(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                              const double *__restrict__ A, int64_t lda, const double *__restrict__ B,
+                              int64_t ldb, double beta, double *__restrict__ C, int64_t ldc) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < M * N;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    int64_t m, n;
+    if (N <= M) { m = e / N; n = e % N; } else { n = e / M; m = e % M; }
+    double acc = 0.0;
+    for (int64_t k = 0; k < K; ++k) {
+      double a = ta ? A[k * lda + m] : A[m * lda + k];
+      double b = tb ? B[n * ldb + k] : B[k * ldb + n];
+      acc = fma(a, b, acc);
+    }
+    double *c = C + m * ldc + n;
+    *c = (beta == 0.0) ? alpha * acc : alpha * acc + beta * (*c);
+  }
+}
+
+// C[i, j] = sum_z W[z][i, j] + beta C[i, j] (fixed order: deterministic)
+__global__ void splitk_reduce(const double *__restrict__ W, int S, int64_t M, int64_t N, double beta,
+                              double *__restrict__ C, int64_t ldc) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < M * N;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    for (int z = 0; z < S; ++z) acc += W[z * M * N + e];
+    double *c = C + (e / N) * ldc + e % N;
+    *c = (beta == 0.0) ? acc : acc + beta * (*c);
+  }
+}
+
+int num_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms;
+}
 }  // namespace
 
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
@@ -91,8 +167,51 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
   }
   IPEPS_REQUIRE((N + BN - 1) / BN <= 2147483647 && (M + BM - 1) / BM <= 65535 && batch <= 65535,
                 "gemm_f64: grid too large");
+  ProfScope prof("dgemm", s, 2.0 * M * N * K * batch,
+                 8.0 * batch * (M * K + K * N + M * N * (beta == 0.0 ? 1.0 : 2.0)));
+  const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
+  const int sms = num_sms();
+  if (batch == 1 && M * N <= 1024 && K >= 256) {
+    int64_t S = std::min<int64_t>(4 * sms, (K + 255) / 256);
+    int64_t kchunk = (K + S - 1) / S;
+    S = (K + kchunk - 1) / kchunk;
+    double *W = static_cast<double *>(dev_alloc(size_t(S) * M * N * sizeof(double), s));
+    multidot_kernel<<<unsigned(S), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, W, kchunk);
+    int rg = int(std::min<int64_t>((M * N + 255) / 256, 4 * sms));
+    splitk_reduce<<<rg, 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
+    count_launch(2);
+    check_launch("dgemm multidot");
+    dev_free(W, s);
+    return;
+  }
+  if (batch == 1 && std::min(M, N) <= 8 && K <= 512) {
+    int rg = int(std::min<int64_t>((M * N + 255) / 256, 16 * sms));
+    perout_kernel<<<rg, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc);
+    count_launch();
+    check_launch("dgemm perout");
+    return;
+  }
+  if (batch == 1 && tiles < sms && K >= 1024) {
+    // few output tiles and a long K: split K over the idle SMs, then reduce
+    int64_t S = std::min<int64_t>((2 * sms + tiles - 1) / tiles, (K + 511) / 512);
+    S = std::min<int64_t>(S, 512);
+    if (S >= 2) {
+      int64_t kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
+      S = (K + kchunk - 1) / kchunk;
+      double *W = static_cast<double *>(dev_alloc(size_t(S) * M * N * sizeof(double), s));
+      dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(S));
+      dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N, kchunk);
+      int64_t n = M * N;
+      int rg = int(std::min<int64_t>((n + 255) / 256, 4 * sms));
+      splitk_reduce<<<rg, 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
+      count_launch(2);
+      check_launch("dgemm splitk");
+      dev_free(W, s);
+      return;
+    }
+  }
   dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(batch));
-  dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC);
+  dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, 0);
   count_launch();
   check_launch("dgemm");
 }

@@ -46,6 +46,7 @@ struct EnvImpl {
   DBuf buf;              // all 8 * Lx * Ly tensors, zero padded to chi
   DBuf spectra;          // last corner spectra (4 * Lx * Ly * chi)
   bool have_spectra = false;
+  std::map<int, DBuf> svd_cache;  // warm starts of the projector SVDs
   cudaStream_t s = nullptr;
   int64_t csize() const { return int64_t(chi) * chi; }
   int64_t esize() const { return int64_t(chi) * cell.D * cell.D * chi; }

@@ -4,6 +4,7 @@
 
 #include "common.h"
 #include "kernels.h"
+#include "profile.h"
 
 namespace ipeps {
 
@@ -151,7 +152,7 @@ __global__ void scale_cols_kernel(int64_t m, int64_t n, const double *__restrict
 }
 
 __global__ void div_scalar_kernel(int64_t n, double *x, const double *nrm) {
-  double inv = 1.0 / (*nrm);
+  double inv = (*nrm != 0.0) ? 1.0 / (*nrm) : 0.0;  // a zero tensor stays zero
   for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
        i += int64_t(gridDim.x) * blockDim.x)
     x[i] *= inv;
@@ -203,6 +204,7 @@ void permute(const double *src, const std::vector<int64_t> &dims, const std::vec
         for (int i = lead; i < k; ++i) rows *= dims[i];
         for (int i = k; i < nd; ++i) cols *= dims[i];
         if (batch <= 65535 && (rows + 31) / 32 <= 65535) {
+          ProfScope prof("permute", s, 0.0, 16.0 * n * (beta == 0.0 ? 1.0 : 1.5));
           dim3 blk(32, 8), grd(unsigned((cols + 31) / 32), unsigned((rows + 31) / 32), unsigned(batch));
           transpose_batched_kernel<<<grd, blk, 0, s>>>(src, dst, rows, cols, batch, alpha, beta);
           count_launch();
@@ -232,6 +234,7 @@ void permute(const double *src, const std::vector<int64_t> &dims, const std::vec
     p.out_dims[k] = dims[perm[k]];
     p.in_stride_for_out[k] = in_stride[perm[k]];
   }
+  ProfScope prof("permute", s, 0.0, 16.0 * n * (beta == 0.0 ? 1.0 : 1.5));
   permute_kernel<<<grid_for(n), 256, 0, s>>>(src, dst, n, p, alpha, beta);
   count_launch();
   check_launch("permute");

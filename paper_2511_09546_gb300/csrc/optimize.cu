@@ -88,6 +88,12 @@ struct Driver {
     IPEPS_CUDA(cudaMemcpyAsync(p.env.buf.p, env0.buf.p, env0.total() * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
     p.env.have_spectra = false;
+    p.env.svd_cache.clear();
+    for (auto &kv : env0.svd_cache) {
+      DBuf b(kv.second.n, s);
+      IPEPS_CUDA(cudaMemcpyAsync(b.p, kv.second.p, kv.second.n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      p.env.svd_cache.emplace(kv.first, std::move(b));
+    }
     double err = INFINITY;
     p.ctm_iters = ctmrg_run(p.env, p.x.p, o.ctm_tol, o.ctm_maxit, Prec(o.prec), &err, s);
     p.ok = err < o.ctm_tol;

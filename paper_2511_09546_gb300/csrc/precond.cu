@@ -10,7 +10,10 @@
 // the unit cell at a time (Sec. IV.B).
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "common.h"
@@ -133,6 +136,13 @@ double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int kr
       gv[j] = cs[j] * gv[j];
       used = j + 1;
       rel = std::fabs(gv[j + 1]) / bnorm;
+      if (std::getenv("IPEPS_DEBUG_GMRES")) {
+        static auto tlast = std::chrono::steady_clock::now();
+        auto tn = std::chrono::steady_clock::now();
+        std::fprintf(stderr, "[ipeps] gmres n=%lld cycle %d step %d rel %.3e (%.1f ms)\n", (long long)n, cycle, j,
+                     rel, std::chrono::duration<double, std::milli>(tn - tlast).count());
+        tlast = tn;
+      }
       if (rel <= rtol || hn == 0.0) break;
       IPEPS_CUDA(cudaMemcpyAsync(V.p + int64_t(j + 1) * n, w.p, n * sizeof(double),
                                  cudaMemcpyDeviceToDevice, s));

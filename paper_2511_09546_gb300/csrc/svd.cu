@@ -17,6 +17,7 @@
 
 #include "common.h"
 #include "kernels.h"
+#include "profile.h"
 
 namespace ipeps {
 
@@ -243,6 +244,7 @@ int jacobi_svd_colmajor(double *G, int64_t m, int64_t n, double *V, cudaStream_t
     IPEPS_CUDA(cudaMemsetAsync(off.p, 0, sizeof(double), s));
     dim3 grd(unsigned(nb / 2), unsigned(batch));
     for (int step = 0; step < nb - 1; ++step) {
+      ProfScope prof("jacobi_pair", s, 0.0, 0.0);
       jacobi_pair_kernel<<<grd, 256, 0, s>>>(Gp.p, m, V ? Vp.p : nullptr, npad, nb, step, tol, off.p);
       count_launch();
     }

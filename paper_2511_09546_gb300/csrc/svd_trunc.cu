@@ -1,0 +1,471 @@
+// Truncated SVD of the opened ring M (N x N) by warm-started subspace
+// iteration, for the forward CTMRG moves (projector truncation, Sec. III.A).
+//
+// Block of k = chi + p vectors.  One iteration:
+//   Y = M V, Q = orth(Y); Z = M^T Q = Qz Rz; Rz = Vg S Ug^T (one-sided block
+//   Jacobi of the k x k factor); U = Q Ug, V = Qz Vg.
+// Orthonormalisation is shifted Cholesky-QR applied three times (one shifted
+// pass, then two plain passes), which is stable for the full dynamic range of
+// M's spectrum; every GEMM is FP64.  The loop stops when M v_i = s_i u_i holds
+// to 1e-13 s_1 for the kept columns.  V is cached per cut and reused by the
+// next CTMRG iteration, so near the fixed point one or two passes suffice.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.h"
+#include "engine.h"
+#include "kernels.h"
+
+namespace ipeps {
+
+namespace {
+
+// A = G + shift * trace(G) * I, then right-looking Cholesky A = R^T R (R upper,
+// row-major).  A pivot below 1e-28 of the largest diagonal marks a direction
+// outside the span: its row of R is set to the unit row (the matching column of
+// Q then carries the vanishing residual).
+__global__ void chol_small_kernel(const double *G, int k, double shift_coef, double *A, double *R,
+                                  int *dead) {
+  __shared__ double piv, dmax;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid == 0) {
+    double tr = 0.0, mx = 0.0;
+    for (int i = 0; i < k; ++i) {
+      tr += G[i * k + i];
+      mx = fmax(mx, G[i * k + i]);
+    }
+    piv = shift_coef * tr;
+    dmax = mx + piv;
+  }
+  __syncthreads();
+  const double sh = piv;
+  for (int e = tid; e < k * k; e += nt) {
+    int i = e / k, j = e % k;
+    A[e] = G[e] + (i == j ? sh : 0.0);
+    R[e] = 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (tid == 0) {
+      double d = A[j * k + j];
+      piv = (d > 1e-28 * dmax) ? sqrt(d) : 0.0;
+      R[j * k + j] = piv > 0.0 ? piv : 1.0;
+      if (dead) dead[j] = (piv == 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    const double p = piv;
+    for (int i = j + 1 + tid; i < k; i += nt) R[j * k + i] = p > 0.0 ? A[j * k + i] / p : 0.0;
+    __syncthreads();
+    const int rem = k - j - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      int i = j + 1 + e / rem, l = j + 1 + e % rem;
+      A[i * k + l] -= R[j * k + i] * R[j * k + l];
+    }
+    __syncthreads();
+  }
+}
+
+// X = R^-1 for upper-triangular R (one thread per column)
+__global__ void tri_inv_kernel(const double *R, int k, double *X) {
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    for (int i = 0; i < k; ++i) X[i * k + c] = 0.0;
+    X[c * k + c] = 1.0 / R[c * k + c];
+    for (int i = c - 1; i >= 0; --i) {
+      double acc = 0.0;
+      for (int l = i + 1; l <= c; ++l) acc += R[i * k + l] * X[l * k + c];
+      X[i * k + c] = -acc / R[i * k + i];
+    }
+  }
+}
+
+__global__ void colnorm_colmajor(const double *X, int64_t m, double *out) {
+  // one block per (contiguous) column of a column-major matrix with m rows
+  int64_t j = blockIdx.x;
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) a += X[j * m + i] * X[j * m + i];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sqrt(sh[0]);
+}
+
+// Ug[r][jj] = Gc[perm[jj]][r] / sig[perm[jj]] (Gc column-major k x k);
+// Vg[r][jj] = Vc[perm[jj]][r]
+__global__ void small_factors_kernel(const double *Gc, const double *Vc, const double *sig, const int *perm,
+                                     int k, double *Ug, double *Vg) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < k * k; e += gridDim.x * blockDim.x) {
+    int r = e / k, jj = e % k, j = perm[jj];
+    double s = sig[j];
+    Ug[e] = s > 0.0 ? Gc[j * k + r] / s : 0.0;
+    Vg[e] = Vc[j * k + r];
+  }
+}
+
+// r_i = |Y_i - s_i U_i| for i < kk (row-major N x k)
+__global__ void residual_kernel(const double *Y, const double *U, const double *S, int64_t N, int64_t k,
+                                double *out) {
+  int64_t j = blockIdx.x;
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < N; i += blockDim.x) {
+    double d = Y[i * k + j] - S[j] * U[i * k + j];
+    a += d * d;
+  }
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = sqrt(sh[0]);
+}
+
+__global__ void zero_dead_cols(double *Q, int64_t N, int k, const int *dead) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < N * k;
+       e += int64_t(gridDim.x) * blockDim.x)
+    if (dead[e % k]) Q[e] = 0.0;
+}
+
+// Y (N x k) -> Q with orthonormal columns and Y = Q R (R upper, k x k) by
+// Cholesky-QR applied `passes` times; the first pass is shifted when shifted.
+// Columns whose pivot vanishes (exact zeros of a padded environment) are
+// marked in dead[] and returned as zero columns.
+void cholqr(const double *Y, int64_t N, int k, double *Q, double *R, int passes, bool shifted, int *dead,
+            cudaStream_t s) {
+  DBuf G(size_t(k) * k, s), A(size_t(k) * k, s), Rp(size_t(k) * k, s), Ri(size_t(k) * k, s),
+      T(size_t(N) * k, s), Racc(size_t(k) * k, s), Rtmp(size_t(k) * k, s);
+  const double eps = 2.220446049250313e-16;
+  const double coef = 11.0 * (double(N) * k + double(k) * (k + 1)) * eps;
+  const double *src = Y;
+  for (int pass = 0; pass < passes; ++pass) {
+    gemm_f64(true, false, k, k, N, 1.0, src, k, src, k, 0.0, G.p, k, s);
+    chol_small_kernel<<<1, 256, 0, s>>>(G.p, k, (pass == 0 && shifted) ? coef : 0.0, A.p, Rp.p, dead);
+    tri_inv_kernel<<<1, 256, 0, s>>>(Rp.p, k, Ri.p);
+    count_launch(2);
+    check_launch("cholqr");
+    double *dst = ((passes - 1 - pass) % 2 == 0) ? Q : T.p;
+    gemm_f64(false, false, N, k, k, 1.0, src, k, Ri.p, k, 0.0, dst, k, s);
+    zero_dead_cols<<<256, 256, 0, s>>>(dst, N, k, dead);
+    count_launch();
+    if (pass == 0) {
+      IPEPS_CUDA(cudaMemcpyAsync(Racc.p, Rp.p, size_t(k) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {  // Racc = Rp Racc
+      gemm_f64(false, false, k, k, k, 1.0, Rp.p, k, Racc.p, k, 0.0, Rtmp.p, k, s);
+      std::swap(Racc, Rtmp);
+    }
+    src = dst;
+  }
+  if (R) IPEPS_CUDA(cudaMemcpyAsync(R, Racc.p, size_t(k) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+}
+
+// column scales 1 / max(s_i, 1e-15 s_0): directions at the rounding floor of M
+// keep bounded norms instead of being blown up (s_0 = x[0], the largest)
+__global__ void recip_kernel(const double *x, int n, double *y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    double floor = 1e-15 * x[0];
+    double v = x[i] > floor ? x[i] : floor;
+    y[i] = v > 0.0 ? 1.0 / v : 1.0;
+  }
+}
+
+}  // namespace
+
+bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, double *U, double *S,
+                  double *V, cudaStream_t s, int *iters) {
+  IPEPS_REQUIRE(k >= chi && k <= N && k % 2 == 0, "svd_subspace: bad block size");
+  // cache layout: V (N x k, row-major) then S (k)
+  DBuf Vc(size_t(N) * k, s), Sc(size_t(k), s), invS(size_t(k), s), Y(size_t(N) * k, s),
+      Q(size_t(N) * k, s), Z(size_t(N) * k, s), Qz(size_t(N) * k, s), Rz(size_t(k) * k, s),
+      Rs(size_t(k) * k, s), Vj(size_t(k) * k, s), sig(size_t(k), s), Ug(size_t(k) * k, s),
+      Vg(size_t(k) * k, s), res(size_t(k), s);
+  int *dflag = static_cast<int *>(dev_alloc(size_t(k) * sizeof(int), s));
+  int *dperm = static_cast<int *>(dev_alloc(size_t(k) * sizeof(int), s));
+  IPEPS_CUDA(cudaMemcpyAsync(Vc.p, cache, size_t(N) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  IPEPS_CUDA(cudaMemcpyAsync(Sc.p, cache + N * k, size_t(k) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  IPEPS_CUDA(cudaMemsetAsync(dflag, 0, size_t(k) * sizeof(int), s));
+  std::vector<double> hs(k), hr(k), sorted(k);
+  IPEPS_CUDA(cudaMemcpyAsync(sorted.data(), Sc.p, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+  std::vector<int> perm(k);
+  const double tol_jac = std::max(1e-14, 10.0 * std::sqrt(double(k)) * 2.220446049250313e-16);
+  int it = 0;
+  const int maxit = 30;
+  bool have = false, ok = true;
+  double prev_worst = INFINITY, prev2 = INFINITY;
+  for (it = 0; it < maxit; ++it) {
+    gemm_f64(false, false, N, k, N, 1.0, M, N, Vc.p, k, 0.0, Y.p, k, s);
+    if (have) {
+      residual_kernel<<<unsigned(chi), 256, 0, s>>>(Y.p, U, S, N, k, res.p);
+      count_launch();
+      IPEPS_CUDA(cudaMemcpyAsync(hr.data(), res.p, chi * sizeof(double), cudaMemcpyDeviceToHost, s));
+      IPEPS_CUDA(cudaStreamSynchronize(s));
+      double worst = 0.0;
+      for (int i = 0; i < chi; ++i)
+        if (sorted[i] > 1e-12 * sorted[0]) worst = std::max(worst, hr[i] / sorted[i]);
+      if (sorted[0] == 0.0 || worst <= 1e-11) break;
+      // stagnation at the rounding floor of M
+      if (it >= 3 && worst > 0.5 * prev2 && worst < 1e-6) break;
+      prev2 = prev_worst;
+      prev_worst = worst;
+    }
+    // scale the columns by the current singular values: Y D^-1 ~ U is well conditioned
+    recip_kernel<<<(k + 127) / 128, 128, 0, s>>>(Sc.p, k, invS.p);
+    count_launch();
+    scale_cols(N, k, Y.p, invS.p, Y.p, s);
+    cholqr(Y.p, N, k, Q.p, nullptr, 2, false, dflag, s);
+    gemm_f64(true, false, N, k, N, 1.0, M, N, Q.p, k, 0.0, Z.p, k, s);
+    scale_cols(N, k, Z.p, invS.p, Z.p, s);
+    cholqr(Z.p, N, k, Qz.p, Rs.p, 2, false, dflag, s);
+    // Z D^-1 = Qz Rs  =>  Z = Qz (Rs D); zero scale factors (dead columns) keep Rs's zero rows
+    scale_cols(k, k, Rs.p, Sc.p, Rz.p, s);
+    // SVD of Rz: one-sided Jacobi on its column-major view Rz^T
+    jacobi_svd_colmajor(Rz.p, k, k, Vj.p, s, tol_jac, 60, 1);
+    colnorm_colmajor<<<unsigned(k), 256, 0, s>>>(Rz.p, k, sig.p);
+    count_launch();
+    IPEPS_CUDA(cudaMemcpyAsync(hs.data(), sig.p, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    std::iota(perm.begin(), perm.end(), 0);
+    std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hs[a] > hs[b]; });
+    for (int i = 0; i < k; ++i) sorted[i] = hs[perm[i]];
+    IPEPS_CUDA(cudaMemcpyAsync(dperm, perm.data(), k * sizeof(int), cudaMemcpyHostToDevice, s));
+    IPEPS_CUDA(cudaMemcpyAsync(S, sorted.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    // Rz^T Vj = Gout => Rz = Vj S Ug^T; Z = M^T Q = (Qz Vj) S Ug^T => M ~ (Q Ug) S (Qz Vj)^T
+    small_factors_kernel<<<64, 256, 0, s>>>(Rz.p, Vj.p, sig.p, dperm, k, Ug.p, Vg.p);
+    count_launch();
+    check_launch("svd_subspace");
+    gemm_f64(false, false, N, k, k, 1.0, Q.p, k, Ug.p, k, 0.0, U, k, s);
+    gemm_f64(false, false, N, k, k, 1.0, Qz.p, k, Vg.p, k, 0.0, V, k, s);
+    IPEPS_CUDA(cudaMemcpyAsync(Vc.p, V, size_t(N) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    IPEPS_CUDA(cudaMemcpyAsync(Sc.p, S, size_t(k) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    have = true;
+    // every direction above the projector cut must be resolved: with fewer than
+    // chi live directions the last live one has to lie below the cut
+    int live = 0;
+    while (live < k && sorted[live] > 0.0) ++live;
+    if (live < chi && live > 0 && sorted[live - 1] > 1e-12 * sorted[0]) {
+      ok = false;
+      break;
+    }
+  }
+  if (ok && have) {
+    IPEPS_CUDA(cudaMemcpyAsync(cache, Vc.p, size_t(N) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    IPEPS_CUDA(cudaMemcpyAsync(cache + N * k, Sc.p, size_t(k) * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  }
+  IPEPS_CUDA(cudaStreamSynchronize(s));
+  dev_free(dflag, s);
+  dev_free(dperm, s);
+  if (iters) *iters = it;
+  return ok && have;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of the top-chi triplets (U, S, V) of M from the k = chi + p computed
+// ones, without the complete basis.  The kept block gets the usual real-SVD
+// formula; the part orthogonal to the kept singular vectors solves, column by
+// column, the symmetric positive-definite system
+//   X s_i - M_perp Y = Gamma_U,  Y s_i - M_perp^T X = Gamma_V,
+// M_perp = (1 - U U^T) M (1 - V V^T), Gamma = the cotangents projected out of
+// the kept block.  The p extra triplets give an explicit first guess (exact
+// on their span), conjugate gradients finish it; M only enters by products.
+namespace {
+
+__global__ void trunc_inner_kernel(const double *A1, const double *B1, const double *S, const double *gS,
+                                   int chi, double *inner) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < chi * chi; e += gridDim.x * blockDim.x) {
+    int i = e / chi, j = e % chi;
+    double v = 0.0;
+    if (i == j) {
+      v = gS ? gS[i] : 0.0;
+    } else {
+      double si = S[i], sj = S[j], diff = sj * sj - si * si;
+      if (diff != 0.0)
+        v = ((A1[i * chi + j] - A1[j * chi + i]) * sj + si * (B1[i * chi + j] - B1[j * chi + i])) / diff;
+    }
+    inner[e] = v;
+  }
+}
+
+// a_ji, b_ji of the explicit part on the extra triplets j (p x chi)
+__global__ void trunc_extra_kernel(const double *ga, const double *gb, const double *S, int chi, int p,
+                                   double *a, double *b) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * chi; e += gridDim.x * blockDim.x) {
+    int j = e / chi, i = e % chi;
+    double si = S[i], sj = S[chi + j], den = si * si - sj * sj;
+    if (den > 0.0 && si > 0.0) {
+      a[e] = (si * ga[e] + sj * gb[e]) / den;
+      b[e] = (sj * ga[e] + si * gb[e]) / den;
+    } else {
+      a[e] = 0.0;
+      b[e] = 0.0;
+    }
+  }
+}
+
+__global__ void safe_recip_kernel(const double *x, int n, double *y) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = x[i] > 0.0 ? 1.0 / x[i] : 0.0;
+}
+
+// per column i: alpha_i = num_i / den_i (0 when den_i <= 0), optional sign
+__global__ void ratio_kernel(const double *num, const double *den, int n, double *out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (den[i] > 0.0 && num[i] > 0.0) ? num[i] / den[i] : 0.0;
+}
+
+// Y[:, i] += sgn * f[i] * X[:, i]  (row-major rows x n)
+__global__ void col_axpy_kernel(int64_t rows, int n, double sgn, const double *f, const double *X, double *Y) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * n;
+       e += int64_t(gridDim.x) * blockDim.x)
+    Y[e] += sgn * f[e % n] * X[e];
+}
+
+// P[:, i] = R[:, i] + f[i] * P[:, i]
+__global__ void col_xpby_kernel(int64_t rows, int n, const double *f, const double *R, double *P) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * n;
+       e += int64_t(gridDim.x) * blockDim.x)
+    P[e] = R[e] + f[e % n] * P[e];
+}
+
+void col_axpy(int64_t rows, int n, double sgn, const double *f, const double *X, double *Y, cudaStream_t s) {
+  col_axpy_kernel<<<512, 256, 0, s>>>(rows, n, sgn, f, X, Y);
+  count_launch();
+}
+
+struct TruncSVDNode : Node {
+  int M, U, S, V;
+  int64_t N;
+  int chi, kb;
+  DBuf Uk, Sk, Vk;  // row-major N x kb, kb
+  void backward(Tape &t) override {
+    double *gU = t.grad(U, false), *gS = t.grad(S, false), *gV = t.grad(V, false);
+    if (!gU && !gS && !gV) return;
+    cudaStream_t s = t.s;
+    const int64_t n = N;
+    const int c = chi, p = kb - chi;
+    const double *Mp = t.vp(M);
+    DBuf zU, zV;
+    if (!gU) { zU = DBuf(size_t(n) * c, s); fill(zU.p, n * c, 0.0, s); gU = zU.p; }
+    if (!gV) { zV = DBuf(size_t(n) * c, s); fill(zV.p, n * c, 0.0, s); gV = zV.p; }
+    DBuf A1(size_t(c) * c, s), B1(size_t(c) * c, s), inner(size_t(c) * c, s), T1(size_t(c) * n, s);
+    // kept block: A1 = U^T gU, B1 = V^T gV (U = first chi columns of Uk, ld kb)
+    gemm_f64(true, false, c, c, n, 1.0, Uk.p, kb, gU, c, 0.0, A1.p, c, s);
+    gemm_f64(true, false, c, c, n, 1.0, Vk.p, kb, gV, c, 0.0, B1.p, c, s);
+    trunc_inner_kernel<<<64, 256, 0, s>>>(A1.p, B1.p, Sk.p, gS, c, inner.p);
+    count_launch();
+    double *gM = t.grad(M);
+    gemm_f64(false, true, c, n, c, 1.0, inner.p, c, Vk.p, kb, 0.0, T1.p, n, s);
+    gemm_f64(false, false, n, n, c, 1.0, Uk.p, kb, T1.p, n, 1.0, gM, n, s);
+    // complement: right-hand sides Gamma (stacked [X; Y] as 2N x chi)
+    DBuf G(size_t(2 * n) * c, s), X(size_t(2 * n) * c, s), R(size_t(2 * n) * c, s), P(size_t(2 * n) * c, s),
+        KP(size_t(2 * n) * c, s), tmp(size_t(n) * c, s), sm(size_t(c) * c, s), invs(size_t(c), s),
+        rr(size_t(c), s), rn(size_t(c), s), pk(size_t(c), s), al(size_t(c), s), bb(size_t(c), s);
+    double *GU = G.p, *GV = G.p + n * c;
+    IPEPS_CUDA(cudaMemcpyAsync(GU, gU, n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    IPEPS_CUDA(cudaMemcpyAsync(GV, gV, n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    gemm_f64(false, false, n, c, c, -1.0, Uk.p, kb, A1.p, c, 1.0, GU, c, s);
+    gemm_f64(false, false, n, c, c, -1.0, Vk.p, kb, B1.p, c, 1.0, GV, c, s);
+    safe_recip_kernel<<<(c + 127) / 128, 128, 0, s>>>(Sk.p, c, invs.p);
+    count_launch();
+    // first guess: explicit on the extra triplets, first order beyond them
+    double *XU = X.p, *XV = X.p + n * c;
+    IPEPS_CUDA(cudaMemcpyAsync(R.p, G.p, 2 * n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (p > 0) {
+      DBuf ga(size_t(p) * c, s), gb(size_t(p) * c, s), a(size_t(p) * c, s), b(size_t(p) * c, s);
+      gemm_f64(true, false, p, c, n, 1.0, Uk.p + c, kb, GU, c, 0.0, ga.p, c, s);
+      gemm_f64(true, false, p, c, n, 1.0, Vk.p + c, kb, GV, c, 0.0, gb.p, c, s);
+      trunc_extra_kernel<<<64, 256, 0, s>>>(ga.p, gb.p, Sk.p, c, p, a.p, b.p);
+      count_launch();
+      // rho = Gamma - (extra block) ga ; X0 = extra a + rho / s
+      gemm_f64(false, false, n, c, p, -1.0, Uk.p + c, kb, ga.p, c, 1.0, R.p, c, s);
+      gemm_f64(false, false, n, c, p, -1.0, Vk.p + c, kb, gb.p, c, 1.0, R.p + n * c, c, s);
+      scale_cols(2 * n, c, R.p, invs.p, X.p, s);
+      gemm_f64(false, false, n, c, p, 1.0, Uk.p + c, kb, a.p, c, 1.0, XU, c, s);
+      gemm_f64(false, false, n, c, p, 1.0, Vk.p + c, kb, b.p, c, 1.0, XV, c, s);
+    } else {
+      scale_cols(2 * n, c, R.p, invs.p, X.p, s);
+    }
+    // K (X, Y) = (X S - Mperp Y, Y S - Mperp^T X)
+    auto K = [&](const double *inX, double *out) {
+      const double *iU = inX, *iV = inX + n * c;
+      double *oU = out, *oV = out + n * c;
+      // Mperp Y: P_U M P_V Y
+      IPEPS_CUDA(cudaMemcpyAsync(tmp.p, iV, n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      gemm_f64(true, false, c, c, n, 1.0, Vk.p, kb, iV, c, 0.0, sm.p, c, s);
+      gemm_f64(false, false, n, c, c, -1.0, Vk.p, kb, sm.p, c, 1.0, tmp.p, c, s);
+      gemm_f64(false, false, n, c, n, 1.0, Mp, n, tmp.p, c, 0.0, oU, c, s);
+      gemm_f64(true, false, c, c, n, 1.0, Uk.p, kb, oU, c, 0.0, sm.p, c, s);
+      gemm_f64(false, false, n, c, c, -1.0, Uk.p, kb, sm.p, c, 1.0, oU, c, s);
+      // Mperp^T X: P_V M^T P_U X
+      IPEPS_CUDA(cudaMemcpyAsync(tmp.p, iU, n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      gemm_f64(true, false, c, c, n, 1.0, Uk.p, kb, iU, c, 0.0, sm.p, c, s);
+      gemm_f64(false, false, n, c, c, -1.0, Uk.p, kb, sm.p, c, 1.0, tmp.p, c, s);
+      gemm_f64(true, false, n, c, n, 1.0, Mp, n, tmp.p, c, 0.0, oV, c, s);
+      gemm_f64(true, false, c, c, n, 1.0, Vk.p, kb, oV, c, 0.0, sm.p, c, s);
+      gemm_f64(false, false, n, c, c, -1.0, Vk.p, kb, sm.p, c, 1.0, oV, c, s);
+      // out = in S - out
+      scale_cols(2 * n, c, inX, Sk.p, out, s, -1.0);
+    };
+    // residual R = G - K X
+    K(X.p, KP.p);
+    IPEPS_CUDA(cudaMemcpyAsync(R.p, G.p, 2 * n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    axpy(2 * n * c, -1.0, KP.p, R.p, s);
+    IPEPS_CUDA(cudaMemcpyAsync(P.p, R.p, 2 * n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    coldot(2 * n, c, G.p, G.p, bb.p, s);
+    coldot(2 * n, c, R.p, R.p, rr.p, s);
+    std::vector<double> hb(c), hr(c);
+    IPEPS_CUDA(cudaMemcpyAsync(hb.data(), bb.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // stop at 1e-12 relative, or when the residual stagnates at the rounding
+    // floor of the small singular values (K is applied through M, whose
+    // rounding is eps |M| against s_i |x|)
+    std::vector<double> hist;
+    for (int it = 0; it < 100; ++it) {
+      IPEPS_CUDA(cudaMemcpyAsync(hr.data(), rr.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+      IPEPS_CUDA(cudaStreamSynchronize(s));
+      double worst = 0.0;
+      for (int i = 0; i < c; ++i)
+        if (hb[i] > 0.0) worst = std::max(worst, std::sqrt(hr[i] / hb[i]));
+      t.svd_iters += 1;
+      hist.push_back(worst);
+      if (worst <= 1e-12) break;
+      if (hist.size() > 4 && worst > 0.5 * hist[hist.size() - 4]) break;
+      K(P.p, KP.p);
+      coldot(2 * n, c, P.p, KP.p, pk.p, s);
+      ratio_kernel<<<(c + 127) / 128, 128, 0, s>>>(rr.p, pk.p, c, al.p);
+      count_launch();
+      col_axpy(2 * n, c, 1.0, al.p, P.p, X.p, s);
+      col_axpy(2 * n, c, -1.0, al.p, KP.p, R.p, s);
+      coldot(2 * n, c, R.p, R.p, rn.p, s);
+      ratio_kernel<<<(c + 127) / 128, 128, 0, s>>>(rn.p, rr.p, c, al.p);  // beta
+      count_launch();
+      col_xpby_kernel<<<512, 256, 0, s>>>(2 * n, c, al.p, R.p, P.p);
+      count_launch();
+      std::swap(rr, rn);
+    }
+    check_launch("trunc_svd_bwd");
+    // gM += X V^T + U Y^T
+    gemm_f64(false, true, n, n, c, 1.0, XU, c, Vk.p, kb, 1.0, gM, n, s);
+    gemm_f64(false, true, n, n, c, 1.0, Uk.p, kb, XV, c, 1.0, gM, n, s);
+  }
+};
+}  // namespace
+
+void push_trunc_svd_node(Tape &t, int M, int U, int S, int V, int64_t N, int chi, int kb, DBuf &&Uk,
+                         DBuf &&Sk, DBuf &&Vk) {
+  auto *nd = new TruncSVDNode;
+  nd->M = M; nd->U = U; nd->S = S; nd->V = V;
+  nd->N = N; nd->chi = chi; nd->kb = kb;
+  nd->Uk = std::move(Uk);
+  nd->Sk = std::move(Sk);
+  nd->Vk = std::move(Vk);
+  t.push(nd);
+}
+
+}  // namespace ipeps

@@ -60,6 +60,10 @@ def lib():
         L.ipeps_last_error.restype = C.c_char_p
         L.ipeps_launch_count.restype = C.c_uint64
         L.ipeps_launch_count.argtypes = [i]
+        L.ipeps_profile.argtypes = [i]
+        L.ipeps_profile_query.argtypes = [C.c_char_p, C.POINTER(C.c_uint64), dp, dp, dp]
+        L.ipeps_profile_query.restype = i
+        L.ipeps_profile_names.restype = C.c_char_p
         L.ipeps_ham_create.argtypes = [i, dp, dp, dp, d, C.POINTER(vp)]
         L.ipeps_ham_heisenberg.argtypes = [i, d, C.POINTER(vp)]
         L.ipeps_ham_kitaev.argtypes = [d, C.POINTER(vp)]
@@ -71,6 +75,9 @@ def lib():
         L.ipeps_energy_grad.argtypes = [sp, vp, vp, vp, dp, vp, vp]
         L.ipeps_precondition.argtypes = [sp, vp, vp, vp, d, i, i, vp, dp, vp]
         L.ipeps_opts_default.argtypes = [C.POINTER(Opts)]
+        i64 = C.c_int64
+        L.ipeps_gemm.argtypes = [i, i, i, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
+        L.ipeps_gemm.restype = i
         L.ipeps_optimize.argtypes = [sp, vp, vp, C.POINTER(Opts), ITER_CB, vp, vp]
         for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ctmrg",
                      "ipeps_env_corner_spectra", "ipeps_energy", "ipeps_energy_grad",
@@ -164,7 +171,7 @@ def ctmrg(A, chi, tol=1e-10, maxit=500, prec=FP64, env=None, allow_unconverged=F
     """CTMRG environment of the cell A.  Returns (env, iterations, final change)."""
     A = _dev(A)
     shape = _shape(A)
-    h = C.c_void_p(env.h if env is not None else None)
+    h = C.c_void_p(env.h.value if env is not None else None)
     it = C.c_int()
     err = C.c_double()
     st = lib().ipeps_ctmrg(C.byref(shape), C.c_void_p(A.data_ptr()), chi, tol, maxit, prec, C.byref(h),
@@ -239,3 +246,39 @@ def optimize(A, ham, opts, callback=None):
 
 def launch_count(reset=False):
     return int(lib().ipeps_launch_count(1 if reset else 0))
+
+
+def profile(enable=True):
+    """Enable (and clear) or disable the library's live kernel timing."""
+    lib().ipeps_profile(1 if enable else 0)
+
+
+def profile_stats():
+    """{kernel class: dict(count, ms, flops, bytes)} since profile(True)."""
+    out = {}
+    names = lib().ipeps_profile_names().decode()
+    for name in [n for n in names.split(",") if n]:
+        cnt = C.c_uint64()
+        ms, fl, by = C.c_double(), C.c_double(), C.c_double()
+        if lib().ipeps_profile_query(name.encode(), C.byref(cnt), C.byref(ms), C.byref(fl), C.byref(by)):
+            out[name] = dict(count=cnt.value, ms=ms.value, flops=fl.value, bytes=by.value)
+    return out
+
+
+def gemm(A, B, ta=False, tb=False, alpha=1.0, beta=0.0, C=None, prec=FP64):
+    """C = alpha op(A) op(B) + beta C with the library's GEMM (2-D float64 CUDA tensors)."""
+    A = _dev(A)
+    B = _dev(B)
+    M, K = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
+    K2, N = (B.shape[1], B.shape[0]) if tb else (B.shape[0], B.shape[1])
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+    _check(lib().ipeps_gemm(prec, int(ta), int(tb), M, N, K, alpha, C_ptr(A), A.shape[1], C_ptr(B), B.shape[1],
+                            beta, C_ptr(C), C.shape[1], _stream()))
+    return C
+
+
+def C_ptr(t):
+    return C.c_void_p(t.data_ptr())
