@@ -112,7 +112,7 @@ def run_ours(args, rank, world, local):
     ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
     prec = ipeps.TF32X3 if args.prec == "tf32x3" else ipeps.FP64
     K, W = args.steps, args.warmup
-    opts = ipeps.default_opts(chi=w["chi"], maxiter=W + K, precondition=1, ctm_tol=1e-10, ctm_maxit=300,
+    opts = ipeps.default_opts(chi=w["chi"], maxiter=W + K, precondition=1, ctm_tol=1e-10, ctm_maxit=120,
                               prec=prec, gtol=0.0)
     A = torch.as_tensor(A_host, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
@@ -122,6 +122,8 @@ def run_ours(args, rank, world, local):
 
     def cb(rec):
         i = rec["iter"]
+        print(f"[bench] iter {i} E={rec['E']:.12f} |g|={rec['gnorm']:.3e} evals={rec['evals']} "
+              f"ctm={rec['ctm_iters']} wall={rec['wall_ms']:.0f} ms", file=sys.stderr, flush=True)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record(stream)
         ends[i] = ev
@@ -163,7 +165,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     host = torch.as_tensor(A_host).pin_memory()
     out_host = torch.empty_like(host).pin_memory()
-    opts_e2e = ipeps.default_opts(chi=w["chi"], maxiter=K, precondition=1, ctm_tol=1e-10, ctm_maxit=300,
+    opts_e2e = ipeps.default_opts(chi=w["chi"], maxiter=1, precondition=1, ctm_tol=1e-10, ctm_maxit=120,
                                   prec=prec, gtol=0.0)
     t0 = time.perf_counter()
     Ad = host.to("cuda", non_blocking=True)
@@ -230,6 +232,47 @@ def run_ours(args, rank, world, local):
     return rec, log
 
 
+def run_passes(args):
+    """--mode pass: W + K hot-path passes at the workload's tensor, each a
+    warm-started CTMRG fixed point + energy + fixed-point gradient + local-metric
+    preconditioner (used for kernel profiles; prints one JSON line)."""
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import inputs, ipeps
+
+    w = inputs.WORKLOADS[args.workload]
+    A0 = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
+    ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+    prec = ipeps.TF32X3 if args.prec == "tf32x3" else ipeps.FP64
+    gen = torch.Generator(device="cpu").manual_seed(1)
+    env, _, _ = ipeps.ctmrg(A0, w["chi"], tol=1e-10, maxit=200, prec=prec, allow_unconverged=True)
+    lat = []
+    for k in range(args.warmup + args.steps):
+        A = A0 + 1e-3 * torch.rand(A0.shape, generator=gen, dtype=torch.float64).cuda()
+        if k == args.warmup:
+            ipeps.profile(True)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        env, it, err = ipeps.ctmrg(A, w["chi"], tol=1e-10, maxit=200, prec=prec, env=env, allow_unconverged=True)
+        E, g = ipeps.energy_grad(A, env, ham)
+        x, res = ipeps.precondition(A, env, g, float((g * g).sum()))
+        t1.record()
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            lat.append(t0.elapsed_time(t1))
+        print(f"[bench] pass {k} ctm {it} E {E:.12f} {t0.elapsed_time(t1):.1f} ms", file=sys.stderr, flush=True)
+    prof = ipeps.profile_stats()
+    rec = {"mode": "pass", "workload": args.workload, "precision": args.prec, "passes": len(lat),
+           "ms_per_pass": statistics.mean(lat) if lat else None,
+           "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3),
+                           "tflops": v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12} for k, v in prof.items()}}
+    print(json.dumps(rec), flush=True)
+
+
 def oracle_sample(workload, n_ctm=1):
     """Oracle time of n_ctm CTMRG iterations at the workload size (seconds each)."""
     import torch
@@ -254,14 +297,18 @@ def oracle_sample(workload, n_ctm=1):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3"])
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass"])
     args = ap.parse_args()
     rank, world, local = _dist()
+    if args.mode == "pass":
+        run_passes(args)
+        return
     if args.impl == "reference":
         if rank != 0:
             return

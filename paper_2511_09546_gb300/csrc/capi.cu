@@ -326,8 +326,10 @@ ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, i
   return guarded([&]() {
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     IPEPS_REQUIRE(M >= 0 && N >= 0 && K >= 0, "gemm: negative size");
-    IPEPS_REQUIRE(A && B && C, "gemm: NULL pointer");
-    IPEPS_REQUIRE(lda >= (ta ? M : K) && ldb >= (tb ? K : N) && ldc >= N, "gemm: leading dimension too small");
+    IPEPS_REQUIRE((A && B) || K == 0, "gemm: NULL operand");
+    IPEPS_REQUIRE(C || M * N == 0, "gemm: NULL output");
+    IPEPS_REQUIRE((lda >= (ta ? M : K) && ldb >= (tb ? K : N)) || K == 0, "gemm: leading dimension too small");
+    IPEPS_REQUIRE(ldc >= N, "gemm: leading dimension of C too small");
     if (prec == IPEPS_TF32X3) ipeps::gemm_tf32x3(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     else if (prec == IPEPS_FP64) ipeps::gemm_f64(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     else throw ipeps::Error(IPEPS_ERR_ARG, "gemm: unknown precision");
