@@ -174,6 +174,26 @@ ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, i
                         const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
                         double *C, int64_t ldc, ipeps_stream_t stream);
 
+/* Allocation-free variant of the FP64 path of ipeps_gemm (no counterpart in
+ * the paper; an interface addition).  Some callers cannot let a library
+ * allocate device memory: a host program whose device memory is already
+ * reserved by another allocator (a new allocation could fail mid-run), or a
+ * loop that must not take the device-wide synchronisation a cudaFree implies.
+ * This call allocates nothing: it splits K over the SMs and keeps the partial
+ * sums in a file-scope device array of 4 Mi doubles (32 MiB) that every GPU
+ * loading the library holds until exit.  The caller passes A, B and C only.
+ * Requires M * N <= 4194304 (returns IPEPS_ERR_ARG with a message
+ * otherwise).  The first call on a device looks up that array's device
+ * address with the device current (make that first call before any stream
+ * capture); later calls reuse it.  The array keeps the last call's partial
+ * sums, each call writes every slice it reads, and calls that overlap on the
+ * GPU (other streams or threads) share the array and race: serialise them.
+ * Arguments and result as ipeps_gemm with prec = IPEPS_FP64.  Synchronises
+ * the stream before returning. */
+ipeps_status ipeps_gemm_noalloc(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                                const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                                double *C, int64_t ldc, ipeps_stream_t stream);
+
 /* ------------------------------------------------------------- misc */
 const char *ipeps_last_error(void);
 /* Kernel launches issued by this thread since the last reset (for reports). */

@@ -338,6 +338,23 @@ ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, i
   });
 }
 
+ipeps_status ipeps_gemm_noalloc(int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
+                                const double *A, int64_t lda, const double *B, int64_t ldb, double beta,
+                                double *C, int64_t ldc, ipeps_stream_t stream) {
+  return guarded([&]() {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(M >= 0 && N >= 0 && K >= 0, "gemm_noalloc: negative size");
+    IPEPS_REQUIRE((A && B) || K == 0, "gemm_noalloc: NULL operand");
+    IPEPS_REQUIRE(C || M * N == 0, "gemm_noalloc: NULL output");
+    IPEPS_REQUIRE((lda >= (ta ? M : K) && ldb >= (tb ? K : N)) || K == 0,
+                  "gemm_noalloc: leading dimension too small");
+    IPEPS_REQUIRE(ldc >= N, "gemm_noalloc: leading dimension of C too small");
+    ipeps::gemm_f64_noalloc(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    return IPEPS_OK;
+  });
+}
+
 void ipeps_opts_default(ipeps_opts *o) {
   if (!o) return;
   o->chi = 16;

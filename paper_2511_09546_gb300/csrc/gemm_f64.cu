@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "common.h"
 #include "kernels.h"
@@ -216,4 +218,81 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
   check_launch("dgemm");
 }
 
+}  // namespace ipeps
+
+// ---------------------------------------------------------------------------
+// Allocation-free split-K GEMM (see ipeps_gemm_noalloc in include/ipeps.h).
+// The split-K partial sums live in this file-scope device array instead of a
+// stream-ordered allocation.  Every slice of it that a call reads is written
+// by the same call first, so nothing needs clearing between calls; calls that
+// overlap on the GPU share the array and race.
+namespace ipeps {
+namespace {
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 22;  // 4 Mi doubles = 32 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+// device address of g_noalloc_scratch for the current device (host code may
+// not use the symbol itself: it is a host-side stand-in, not a device address)
+double *noalloc_scratch_ptr() {
+  static double *ptrs[64] = {nullptr};
+  static std::mutex mu;
+  int dev = 0;
+  IPEPS_CUDA(cudaGetDevice(&dev));
+  IPEPS_REQUIRE(dev >= 0 && dev < 64, "gemm_noalloc: device index out of range");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      throw Error(IPEPS_ERR_CUDA, std::string("gemm_noalloc: cudaGetSymbolAddress failed: ") +
+                                      cudaGetErrorString(e));
+    ptrs[dev] = static_cast<double *>(p);
+  }
+  return ptrs[dev];
+}
+
+__global__ void scale_matrix_kernel(int64_t M, int64_t N, double beta, double *C, int64_t ldc) {
+  for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < M * N;
+       e += int64_t(gridDim.x) * blockDim.x) {
+    double *c = C + (e / N) * ldc + e % N;
+    *c = (beta == 0.0) ? 0.0 : beta * (*c);
+  }
+}
+}  // namespace
+
+void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                      int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                      cudaStream_t s) {
+  IPEPS_REQUIRE(M >= 0 && N >= 0 && K >= 0, "gemm_noalloc: negative size");
+  if (M == 0 || N == 0) return;
+  IPEPS_REQUIRE(M * N <= kNoAllocScratchDoubles,
+                "gemm_noalloc: M*N = " + std::to_string(M * N) + " exceeds the scratch of " +
+                    std::to_string(kNoAllocScratchDoubles) + " doubles (32 MiB)");
+  const int sms = num_sms();
+  if (K == 0) {
+    scale_matrix_kernel<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(M, N, beta, C, ldc);
+    check_launch("gemm_noalloc scale");
+    return;
+  }
+  double *W = noalloc_scratch_ptr();
+  const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM);
+  const int64_t fit = kNoAllocScratchDoubles / (M * N);  // slices that fit in the scratch
+  if (M * N <= 1024 && K >= 256) {
+    int64_t S = std::min<int64_t>({int64_t(4) * sms, (K + 255) / 256, fit});
+    int64_t kchunk = (K + S - 1) / S;
+    S = (K + kchunk - 1) / kchunk;
+    multidot_kernel<<<unsigned(S), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, W, kchunk);
+    splitk_reduce<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
+    check_launch("gemm_noalloc multidot");
+    return;
+  }
+  int64_t S = std::max<int64_t>(1, std::min<int64_t>({(2 * sms + tiles - 1) / tiles, (K + 511) / 512, fit, int64_t(512)}));
+  int64_t kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
+  S = (K + kchunk - 1) / kchunk;
+  IPEPS_REQUIRE((M + BM - 1) / BM <= 65535, "gemm_noalloc: grid too large");
+  dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(S));
+  dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N, kchunk);
+  splitk_reduce<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
+  check_launch("gemm_noalloc splitk");
+}
 }  // namespace ipeps

@@ -44,6 +44,12 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
               int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
               cudaStream_t s, int64_t batch = 1, int64_t sA = 0, int64_t sB = 0, int64_t sC = 0);
 
+// gemm_f64 without any device allocation: split-K partial sums in a static
+// device array (see ipeps_gemm_noalloc)
+void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                      int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
+                      cudaStream_t s);
+
 // One-sided block Jacobi SVD of `batch` column-major m x n matrices G (ld = m,
 // matrix stride m*n): on return G holds U S (orthogonal columns) and, if V is
 // not null, V (n x n column-major per matrix, stride n*n) the accumulated

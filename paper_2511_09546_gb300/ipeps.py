@@ -78,6 +78,8 @@ def lib():
         i64 = C.c_int64
         L.ipeps_gemm.argtypes = [i, i, i, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
         L.ipeps_gemm.restype = i
+        L.ipeps_gemm_noalloc.argtypes = [i, i, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
+        L.ipeps_gemm_noalloc.restype = i
         L.ipeps_optimize.argtypes = [sp, vp, vp, C.POINTER(Opts), ITER_CB, vp, vp]
         for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ctmrg",
                      "ipeps_env_corner_spectra", "ipeps_energy", "ipeps_energy_grad",
@@ -282,3 +284,13 @@ def gemm(A, B, ta=False, tb=False, alpha=1.0, beta=0.0, C=None, prec=FP64):
 
 def C_ptr(t):
     return C.c_void_p(t.data_ptr())
+
+
+def gemm_noalloc(A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0):
+    """C = alpha op(A) op(B) + beta C through the allocation-free FP64 entry point
+    (C is written in place; the library allocates no device memory for it)."""
+    M, K = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
+    N = B.shape[0] if tb else B.shape[1]
+    _check(lib().ipeps_gemm_noalloc(int(ta), int(tb), M, N, K, alpha, C_ptr(A), A.shape[1], C_ptr(B),
+                                    B.shape[1], beta, C_ptr(C), C.shape[1], _stream()))
+    return C
