@@ -294,6 +294,45 @@ def oracle_sample(workload, n_ctm=1):
     return dt, torch.get_num_threads()
 
 
+def run_gemm(args):
+    """--mode gemm: the 3xTF32 tcgen05 GEMM on n x n x n FP64 operands, timed per
+    kernel class with CUDA events (W warm-up calls, K timed calls)."""
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import ipeps
+
+    n = args.gemm_n
+    g = torch.Generator(device="cpu").manual_seed(0)
+    A = torch.randn((n, n), generator=g, dtype=torch.float64).cuda()
+    B = torch.randn((n, n), generator=g, dtype=torch.float64).cuda()
+    C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        ipeps.gemm(A, B, C=C, prec=ipeps.TF32X3)
+    torch.cuda.synchronize()
+    ipeps.profile(True)
+    for _ in range(args.steps):
+        ipeps.gemm(A, B, C=C, prec=ipeps.TF32X3)
+    torch.cuda.synchronize()
+    st = ipeps.profile_stats()
+    ipeps.profile(False)
+    ref_rows = A[:64] @ B
+    err = float((C[:64] - ref_rows).abs().max() / ref_rows.abs().max())
+    peaks = _peaks()
+    tf32_peak = peaks.get("bf16_tflops", 1885.7) / 2.0
+    gm, pk = st.get("tc_gemm", {}), st.get("tc_pack", {})
+    logical = gm["flops"] / (gm["ms"] * 1e-3) / 1e12
+    rec = {"mode": "gemm", "n": n, "launches": gm.get("count"), "gemm_ms": gm["ms"] / max(1, gm["count"]),
+           "pack_ms": pk.get("ms", 0.0) / max(1, pk.get("count", 1)),
+           "logical_tflops": logical, "issued_tf32_tflops": 3 * logical,
+           "tf32_peak_tflops": tf32_peak, "issued_frac_of_tf32_peak": 3 * logical / tf32_peak,
+           "pack_gbs": pk.get("bytes", 0.0) / max(1e-9, pk.get("ms", 0.0) * 1e-3) / 1e9,
+           "rel_err_vs_fp64": err}
+    print(json.dumps(rec), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -303,11 +342,15 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3"])
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass"])
+    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass", "gemm"])
+    ap.add_argument("--gemm-n", type=int, default=8192)
     args = ap.parse_args()
     rank, world, local = _dist()
     if args.mode == "pass":
         run_passes(args)
+        return
+    if args.mode == "gemm":
+        run_gemm(args)
         return
     if args.impl == "reference":
         if rank != 0:

@@ -31,6 +31,15 @@
 
 namespace ipeps {
 
+double sv_cutoff(Prec prec) {
+  if (prec == Prec::FP64) return kSvCutoff;
+  static const double c = [] {
+    const char *e = std::getenv("IPEPS_SV_CUTOFF_TF32X3");
+    return e ? std::atof(e) : 1e-7;
+  }();
+  return c;
+}
+
 namespace {
 int rot_name(int n) { return n < 4 ? (n + 1) % 4 : 4 + (n - 4 + 1) % 4; }
 
@@ -157,7 +166,7 @@ void left_move(Tape &t, const Cell &c, int chi, StateVars &sv, int r) {
       int U, S, V;
       t.vkey = (r * 64 + x) * 64 + y;
       t_svd(t, M, std::min(chi, N), &U, &S, &V);
-      int fs = t_inv_sqrt_cut(t, S, kSvCutoff);
+      int fs = t_inv_sqrt_cut(t, S, sv_cutoff(t.prec));
       Pup[x * Ly + y] = t_scale_cols(t, t_contract(t, R2, "ba", U, "bk", "ak"), fs);
       Pdn[x * Ly + y] = t_scale_cols(t, t_contract(t, R1, "ab", V, "bk", "ak"), fs);
     }
@@ -285,6 +294,7 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
               cudaStream_t s) {
   const Cell &c = e.cell;
   const int nmat = 4 * c.nsites();
+  e.prec = prec;
   if (!e.have_spectra) corner_spectra(e, s);
   DBuf prev(size_t(nmat) * e.chi, s);
   double change = INFINITY;

@@ -17,6 +17,16 @@
 namespace ipeps {
 
 // ------------------------------------------------------------------ contract
+// The tensor-core path pads M and N to 128 and K to 32 and adds a pack pass;
+// below a few million multiply-adds, or when padding would waste more than
+// half of the tile, the FP64 kernels are faster and exact.
+bool tc_worthwhile(int64_t m, int64_t n, int64_t k) {
+  if (m < 64 || n < 64 || k < 32) return false;
+  const double mp = double((m + 127) / 128 * 128), np = double((n + 127) / 128 * 128);
+  const double kp = double((k + 31) / 32 * 32);
+  return double(m) * n * k >= double(1 << 24) && double(m) * n * k >= 0.5 * mp * np * kp;
+}
+
 void contract(const Ten &A, const std::string &la, const Ten &B, const std::string &lb, const Ten &C,
               const std::string &lc, cudaStream_t s, double alpha, double beta, Prec prec) {
   IPEPS_REQUIRE(la.size() == A.d.size() && lb.size() == B.d.size() && lc.size() == C.d.size(),
@@ -85,7 +95,7 @@ void contract(const Ten &A, const std::string &la, const Ten &B, const std::stri
     Cp = Cb.p;
   }
   double ga = direct ? alpha : 1.0, gb = direct ? beta : 0.0;
-  if (prec == Prec::TF32X3) gemm_tf32x3(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
+  if (prec == Prec::TF32X3 && tc_worthwhile(m, n, k)) gemm_tf32x3(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
   else gemm_f64(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
   if (!direct) permute(Cp, dims_of(FA + FB), perm_to(FA + FB, lc), C.p, s, alpha, beta);
 }

@@ -1,10 +1,463 @@
-// 3xTF32 tensor-core GEMM (tcgen05) -- placeholder until the kernel lands.
+// 3xTF32 GEMM on the fifth-generation tensor cores (tcgen05, sm_103a).
+//
+// The bulk contractions of the split-precision path: C = alpha op(A) op(B) +
+// beta C with FP64 operands and result.  Each operand is split x = hi + lo
+// with hi = tf32(x) and lo = tf32(x - hi); the product
+// A B ~ A_hi B_hi + A_hi B_lo + A_lo B_hi is one TF32 GEMM over a tripled K:
+//   A' = [A_hi | A_hi | A_lo]   (M x 3K, K-major)
+//   B' = [B_hi | B_lo | B_hi]   (N x 3K, K-major)
+// written by one tiled pack kernel that also absorbs the transposes of op(A),
+// op(B).
+//
+// Accumulation.  The tensor core rounds its FP32 accumulator toward zero
+// after every MMA, so one accumulator run over the whole of K carries an error
+// that grows linearly in K/8 and is biased; at K = 8192 that error is as large
+// as dropping the lo terms altogether.  The kernel therefore accumulates only
+// `chunk` K slices in TMEM, then adds the chunk's partial sums into a
+// compensated (two-sum) FP32 pair per output, also kept in TMEM, so the
+// truncation bias no longer builds up across chunks.  Two TMEM accumulators
+// alternate, so the MMAs of one chunk overlap the flush of the previous one.
+//
+// Roles (one CTA per 128 x 128 output tile, 10 warps):
+//   * warps 0-7 flush and write the result: warp w reads TMEM lanes
+//     32 (w % 4) .. +31 (its rows) and columns 64 (w / 4) .. +63;
+//   * lane 0 of warp 8 streams 32-wide K slices of A' and B' with TMA (128-byte
+//     swizzle) into a ring of shared-memory stages guarded by mbarriers; warp 8
+//     also owns the TMEM allocation: two accumulators, then the hi and lo
+//     halves of the compensated sums (4 x 128 = 512 columns);
+//   * lane 0 of warp 9 issues tcgen05.mma (M = 128, N = 128, K = 8, four per
+//     slice), releases each stage with tcgen05.commit and signals each
+//     finished chunk on the accumulator's mbarrier.
+// Every mbarrier wait is bounded: on expiry the kernel raises an error word,
+// skips the write of C, drains its own copies (again bounded), frees its TMEM
+// and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstdlib>
+#include <string>
+
 #include "common.h"
 #include "engine.h"
+#include "kernels.h"
+#include "profile.h"
 
 namespace ipeps {
-void gemm_tf32x3(bool, bool, int64_t, int64_t, int64_t, double, const double *, int64_t, const double *,
-                 int64_t, double, double *, int64_t, cudaStream_t) {
-  throw Error(IPEPS_ERR_ARG, "3xTF32 tensor-core GEMM is not available in this build");
+
+namespace {
+
+constexpr int BM = 128;          // rows per tile (TMEM lanes)
+constexpr int BN = 128;          // columns per tile (TMEM columns per accumulator)
+constexpr int BKT = 32;          // TF32 elements per K slice = 128 bytes (one swizzle row)
+constexpr int STAGES = 6;        // shared-memory ring: 6 x 32 KB
+constexpr int FLUSH_WARPS = 8;   // warps 0-7
+constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
+constexpr int THREADS = 32 * (FLUSH_WARPS + 2);
+constexpr int WCOLS = BN / 2;    // accumulator columns per flush warp
+constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the phase with the given parity; false (and *err set) on expiry
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, long long limit = kWaitCycles) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > limit) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
+      : "memory");
+}
+
+// K-major operand tile of rows x 128 bytes, 128-byte swizzle, 8-row groups 1024 bytes apart
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr >> 4) & 0x3FFF);  // start address
+  d |= uint64_t(1) << 16;                // leading byte offset (unused for swizzled K-major)
+  d |= uint64_t(1024 >> 4) << 32;        // stride byte offset: 8 rows x 128 B
+  d |= uint64_t(1) << 46;                // descriptor version
+  d |= uint64_t(2) << 61;                // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// tcgen05.ld of 32 lanes x 16 columns without the wait; tmem_ld_wait then ties
+// the registers to the completion so that no use can move above it
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15])
+               :
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   int64_t M, int64_t N, int nk, int chunk, double alpha, double beta,
+                   double *__restrict__ C, int64_t ldc, int *err) {
+  constexpr uint32_t A_BYTES = BM * BKT * 4, B_BYTES = BN * BKT * 4;
+  extern __shared__ uint8_t smem_raw[];
+  // 1024-byte aligned ring of stages: [A stage | B stage] x STAGES
+  uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nchunks = (nk + chunk - 1) / chunk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], FLUSH_WARPS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == PRODUCER_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(uint32_t(4 * BN))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+
+  int issued = 0;  // K slices whose loads lane 0 of the producer warp started
+  if (warp == PRODUCER_WARP) {
+    if (lane == 0) {
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES;
+        if (!mbar_wait(&empty[s], ((kt / STAGES) & 1) ^ 1, err)) break;
+        uint8_t *sa = base + size_t(s) * (A_BYTES + B_BYTES);
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        tma_load_2d(sa, &mapA, &full[s], kt * BKT, m0);
+        tma_load_2d(sa + A_BYTES, &mapB, &full[s], kt * BKT, n0);
+        issued = kt + 1;
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(BN >> 3) << 17) |
+                                 (uint32_t(BM >> 4) << 24);
+      bool ok = true;
+      int kt = 0;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1, use = c >> 1;
+        ok = mbar_wait(&acc_empty[b], (use & 1) ^ 1, err);
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + uint32_t(b * BN);
+        const int k_first = kt, k_end = min(nk, kt + chunk);
+        for (; kt < k_end; ++kt) {
+          const int s = kt % STAGES;
+          ok = mbar_wait(&full[s], (kt / STAGES) & 1, err);
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          uint8_t *sa = base + size_t(s) * (A_BYTES + B_BYTES);
+          const uint64_t ad = smem_desc(smem_u32(sa)), bd = smem_desc(smem_u32(sa + A_BYTES));
+#pragma unroll
+          for (int ks = 0; ks < BKT / 8; ++ks)  // 8 TF32 = 32 bytes per MMA: +2 in the address field
+            mma_tf32(acc, ad + 2 * ks, bd + 2 * ks, idesc, (kt != k_first || ks != 0) ? 1u : 0u);
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[b]);
+      }
+    }
+  } else {
+    // ---- flush warps: chunk partials (TMEM, FP32) -> compensated pair (hi, lo), also in TMEM
+    const uint32_t lanes = uint32_t((warp & 3) * 32) << 16, cw = uint32_t((warp >> 2) * WCOLS);
+    const uint32_t t_acc = tmem + lanes + cw, t_hi = tmem + lanes + 2 * BN + cw, t_lo = t_hi + BN;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1, use = c >> 1;
+      ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], use & 1, err) ? 1 : 0) != 0;
+      if (!ok) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int q = 0; q < WCOLS / 16; ++q) {
+        uint32_t v[16], h[16], l[16];
+        tmem_ld16_issue(t_acc + uint32_t(b * BN + q * 16), v);
+        if (c > 0) {
+          tmem_ld16_issue(t_hi + uint32_t(q * 16), h);
+          tmem_ld16_issue(t_lo + uint32_t(q * 16), l);
+          tmem_ld_wait(v);
+          tmem_ld_wait(h);
+          tmem_ld_wait(l);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            // two-sum: hi + x = sum + e exactly
+            const float x = __uint_as_float(v[j]), hv = __uint_as_float(h[j]);
+            const float sum = hv + x, bv = sum - hv;
+            const float e = (hv - (sum - bv)) + (x - bv);
+            h[j] = __float_as_uint(sum);
+            l[j] = __float_as_uint(__uint_as_float(l[j]) + e);
+          }
+        } else {
+          tmem_ld_wait(v);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            h[j] = v[j];
+            l[j] = 0u;
+          }
+        }
+        tmem_st16(t_hi + uint32_t(q * 16), h);
+        tmem_st16(t_lo + uint32_t(q * 16), l);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+    if (ok) {
+      const int64_t row = m0 + (warp & 3) * 32 + lane;
+      const int64_t col0 = n0 + (warp >> 2) * WCOLS;
+#pragma unroll 1
+      for (int q = 0; q < WCOLS / 16; ++q) {
+        uint32_t h[16], l[16];
+        tmem_ld16_issue(t_hi + uint32_t(q * 16), h);
+        tmem_ld16_issue(t_lo + uint32_t(q * 16), l);
+        tmem_ld_wait(h);
+        tmem_ld_wait(l);
+        if (row < M) {
+          double *crow = C + row * ldc + col0 + q * 16;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (col0 + q * 16 + j < N) {
+              const double out = alpha * (double(__uint_as_float(h[j])) + double(__uint_as_float(l[j])));
+              crow[j] = (beta == 0.0) ? out : out + beta * crow[j];
+            }
+          }
+        }
+      }
+    }
+  }
+  // on an error path, let this CTA's copies land before the shared memory goes away
+  if (warp == PRODUCER_WARP && lane == 0 && issued > 0 && *err) {
+    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+      mbar_wait(&full[kt % STAGES], (kt / STAGES) & 1, err, 200000000ll);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == PRODUCER_WARP) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(4 * BN))
+                 : "memory");
+  }
+}
+
+// tf32(x): round-to-nearest to 10 explicit mantissa bits, kept in an FP32 container
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// P[r][seg * Kp + k] for r < rows_pad, k < Kp: segment pattern (hi, hi, lo) for A
+// (pattern 0) or (hi, lo, hi) for B (pattern 1); source element (r, k) of op(X)
+// is X[k * ld + r] when trans, X[r * ld + k] otherwise; zero outside (rows, K).
+// One 256-thread block per 32 x 32 tile: coalesced reads along whichever index
+// is contiguous in X, a shared-memory transpose, coalesced writes along k.
+__global__ void __launch_bounds__(256) split_pack_kernel(const double *__restrict__ X, int64_t ld, bool trans,
+                                                         int64_t rows, int64_t K, int64_t Kp, int pattern,
+                                                         float *__restrict__ P) {
+  __shared__ double T[32][33];  // T[k][r]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t k0 = int64_t(blockIdx.x) * 32, r0 = int64_t(blockIdx.y) * 32;
+#pragma unroll
+  for (int i = 0; i < 32; i += 8) {
+    if (trans) {
+      const int64_t k = k0 + ty + i, r = r0 + tx;
+      T[ty + i][tx] = (k < K && r < rows) ? X[k * ld + r] : 0.0;
+    } else {
+      const int64_t r = r0 + ty + i, k = k0 + tx;
+      T[tx][ty + i] = (k < K && r < rows) ? X[r * ld + k] : 0.0;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 32; i += 8) {
+    const int r = ty + i;
+    const double x = T[tx][r];
+    const float hi = to_tf32(float(x));
+    const float lo = to_tf32(float(x - double(hi)));
+    float *row = P + (r0 + r) * (3 * Kp) + k0 + tx;
+    row[0] = hi;
+    row[Kp] = (pattern == 0) ? hi : lo;
+    row[2 * Kp] = (pattern == 0) ? lo : hi;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+      throw Error(IPEPS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const float *P, int64_t rows_pad, int64_t Kt, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t dims[2] = {cuuint64_t(Kt), cuuint64_t(rows_pad)};
+  cuuint64_t strides[1] = {cuuint64_t(Kt) * 4};
+  cuuint32_t box[2] = {cuuint32_t(BKT), cuuint32_t(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(P), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(IPEPS_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(int(r)));
+  return m;
+}
+
+int *error_word(cudaStream_t s) {
+  static int *w = nullptr;
+  if (!w) IPEPS_CUDA(cudaMalloc(&w, sizeof(int)));
+  IPEPS_CUDA(cudaMemsetAsync(w, 0, sizeof(int), s));
+  return w;
+}
+
+void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, int nk, int chunk, double alpha,
+            double beta, double *C, int64_t ldc, int *err, cudaStream_t s) {
+  constexpr size_t smem = size_t(STAGES) * (BM + BN) * BKT * 4 + 1024;
+  static bool attr = false;
+  if (!attr) {
+    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    attr = true;
+  }
+  dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM));
+  tc_gemm_kernel<<<grd, THREADS, smem, s>>>(ma, mb, M, N, nk, chunk, alpha, beta, C, ldc, err);
+  count_launch();
+  check_launch("tc_gemm");
+}
+
+int chunk_slices() {
+  // K slices (32 TF32 elements of the tripled K) per TMEM accumulation chunk
+  static int c = [] {
+    const char *e = std::getenv("IPEPS_TC_CHUNK");
+    int v = e ? std::atoi(e) : 4;
+    return v < 1 ? 1 : v;
+  }();
+  return c;
+}
+
+}  // namespace
+
+void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                 const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s) {
+  if (M <= 0 || N <= 0) return;
+  if (K <= 0) {
+    gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);  // C = beta C
+    return;
+  }
+  IPEPS_REQUIRE((M + BM - 1) / BM <= 65535, "tc_gemm: M too large");
+  const int64_t Kp = (K + BKT - 1) / BKT * BKT, Kt = 3 * Kp;
+  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN;
+  IPEPS_REQUIRE(Kt / BKT <= 2147483647 && Kp / 32 <= 2147483647, "tc_gemm: K too large");
+  float *Ap = static_cast<float *>(dev_alloc(size_t(Mp) * Kt * sizeof(float), s));
+  float *Bp = static_cast<float *>(dev_alloc(size_t(Np) * Kt * sizeof(float), s));
+  {
+    ProfScope prof("tc_pack", s, 0.0, 8.0 * (M * K + K * N) + 12.0 * (Mp + Np) * Kp);
+    // op(A)[m, k]: A stored M x K (lda) or, transposed, K x M
+    split_pack_kernel<<<dim3(unsigned(Kp / 32), unsigned(Mp / 32)), 256, 0, s>>>(A, lda, ta, M, K, Kp, 0, Ap);
+    // op(B)[k, n] as rows n of B': B stored K x N (ldb), i.e. element (n, k) at B[k * ldb + n]
+    // (trans view) or, when tb, N x K with element (n, k) at B[n * ldb + k]
+    split_pack_kernel<<<dim3(unsigned(Kp / 32), unsigned(Np / 32)), 256, 0, s>>>(B, ldb, !tb, N, K, Kp, 1, Bp);
+    count_launch(2);
+    check_launch("tc_pack");
+  }
+  const CUtensorMap ma = make_map(Ap, Mp, Kt, BM);
+  const CUtensorMap mb = make_map(Bp, Np, Kt, BN);
+  int *err = error_word(s);
+  {
+    ProfScope prof("tc_gemm", s, 2.0 * M * N * K, 4.0 * (Mp + Np) * Kt + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
+    launch(ma, mb, M, N, int(Kt / BKT), chunk_slices(), alpha, beta, C, ldc, err, s);
+  }
+  int h = 0;
+  IPEPS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  dev_free(Ap, s);
+  dev_free(Bp, s);
+  IPEPS_CUDA(cudaStreamSynchronize(s));
+  if (h) throw Error(IPEPS_ERR_TIMEOUT, "tc_gemm: an mbarrier wait expired");
+}
+
 }  // namespace ipeps

@@ -35,3 +35,47 @@ def test_gemm_f64(ip, M, N, K, ta, tb):
     out = ip.gemm(A, B, ta=ta, tb=tb, alpha=0.7, beta=-0.3, C=C0.clone())
     scale = max(1.0, float(ref.abs().max()))
     assert float((out - ref).abs().max()) <= 1e-12 * scale * max(1, K) ** 0.5
+
+
+TC_SHAPES = [(128, 128, 32), (130, 70, 33), (256, 256, 256), (1000, 300, 777), (300, 1000, 96), (1, 5, 40),
+             (257, 129, 2049)]
+TRANS = [(False, False), (True, False), (False, True), (True, True)]
+
+
+def _operands(M, N, K, ta, tb, seed, kind):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    sa, sb = ((K, M) if ta else (M, K)), ((N, K) if tb else (K, N))
+    if kind == "int":
+        A = torch.randint(-4, 5, sa, generator=g).double()
+        B = torch.randint(-4, 5, sb, generator=g).double()
+    else:
+        A = torch.randn(sa, generator=g, dtype=torch.float64)
+        B = torch.randn(sb, generator=g, dtype=torch.float64)
+    C0 = torch.randint(-4, 5, (M, N), generator=g).double()
+    return A.cuda(), B.cuda(), C0.cuda()
+
+
+@pytest.mark.parametrize("M,N,K", TC_SHAPES)
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_gemm_tf32x3_integers_exact(ip, M, N, K, ta, tb):
+    # small integers are exact in TF32 (lo = 0) and every partial sum here is an
+    # integer below 2^24, so the tensor-core result must be exact: this pins
+    # the pack layout, the transposes, the tails and the tile indexing bit for bit
+    A, B, C0 = _operands(M, N, K, ta, tb, M * 7 + N * 3 + K, "int")
+    ref = 2.0 * ((A.T if ta else A) @ (B.T if tb else B)) - C0
+    out = ip.gemm(A, B, ta=ta, tb=tb, alpha=2.0, beta=-1.0, C=C0.clone(), prec=ip.TF32X3)
+    assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("M,N,K", TC_SHAPES)
+@pytest.mark.parametrize("ta,tb", TRANS)
+def test_gemm_tf32x3_random(ip, M, N, K, ta, tb):
+    # 3xTF32: dropping lo*lo costs ~2^-22 |a||b| per product; FP32 accumulation in
+    # chunks (truncated per MMA) with a compensated sum across chunks stays near
+    # 2^-21 of sum |a||b|.  A dropped correction term (error ~2^-12) fails this.
+    A, B, C0 = _operands(M, N, K, ta, tb, M * 11 + N * 5 + K, "randn")
+    opA, opB = (A.T if ta else A), (B.T if tb else B)
+    ref = 1.3 * (opA @ opB) + 0.25 * C0
+    out = ip.gemm(A, B, ta=ta, tb=tb, alpha=1.3, beta=0.25, C=C0.clone(), prec=ip.TF32X3)
+    scale = 1.3 * (opA.abs() @ opB.abs())
+    assert float(((out - ref).abs() / scale).max()) <= 2.0 ** -19
