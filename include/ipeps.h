@@ -48,10 +48,23 @@ typedef enum {
 } ipeps_status;
 
 typedef enum {
-  IPEPS_FP64 = 0,    /* every contraction in FP64 */
-  IPEPS_TF32X3 = 1   /* bulk contraction GEMMs as 3xTF32 on tcgen05 tensor cores,
-                        FP32 accumulate; projectors, normalisation, convergence,
-                        gradient adjoint and preconditioner stay FP64 */
+  IPEPS_FP64 = 0,       /* every contraction in FP64 */
+  IPEPS_TF32X3 = 1,     /* split precision: enlarged corners, half-system products
+                           and absorption as 3xTF32 GEMMs on tcgen05 tensor cores
+                           (FP32 accumulation in chunks, compensated across them);
+                           the four-corner product, the projector products and
+                           their truncated SVD, normalisation, the convergence
+                           test, the gradient adjoint and the preconditioner stay
+                           FP64.  CTMRG runs split-precision iterations until the
+                           spectra change < 1e-6 (or stops improving), then FP64
+                           iterations until tol: the fixed point, energy and
+                           gradient are those of the FP64 path. */
+  IPEPS_TF32X3_ALL = 2  /* throughput mode for large chi D^2: every bulk GEMM,
+                           the four-corner and projector products included, and
+                           the adjoint's GEMMs as 3xTF32; SVD, normalisation and
+                           preconditioner FP64; no FP64 phase, so the spectra
+                           change stalls near the 3xTF32 noise floor and a tol
+                           below it ends in IPEPS_ERR_NOT_CONVERGED */
 } ipeps_prec;
 
 typedef struct {

@@ -53,7 +53,7 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   // ---- F tape at e*
   Tape tF(s);
   tF.vcache = &e.svd_cache;
-  tF.prec = e.prec;  // the fixed-point map's bulk GEMMs in the precision CTMRG ran in
+  tF.prec = e.prec;  // the fixed-point map in the precision of the last CTMRG iterations
   StateVars in = state_leaves(tF, e, A_dev);
   StateVars out = in;
   ctmrg_iteration(tF, c, e.chi, out);

@@ -214,7 +214,7 @@ ipeps_status ipeps_ctmrg(const ipeps_shape *shape, const double *A_dev, int chi,
     IPEPS_REQUIRE(A_dev && inout_env, "ctmrg: NULL argument");
     IPEPS_REQUIRE(chi >= 1 && chi <= 4096, "ctmrg: chi out of range");
     IPEPS_REQUIRE(maxit >= 0 && tol >= 0.0, "ctmrg: bad tol / maxit");
-    IPEPS_REQUIRE(prec == IPEPS_FP64 || prec == IPEPS_TF32X3, "ctmrg: unknown precision");
+    IPEPS_REQUIRE(prec == IPEPS_FP64 || prec == IPEPS_TF32X3 || prec == IPEPS_TF32X3_ALL, "ctmrg: unknown precision");
     check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
     std::unique_ptr<ipeps_env_s> fresh;
     ipeps_env env = *inout_env;
@@ -330,7 +330,7 @@ ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, i
     IPEPS_REQUIRE(C || M * N == 0, "gemm: NULL output");
     IPEPS_REQUIRE((lda >= (ta ? M : K) && ldb >= (tb ? K : N)) || K == 0, "gemm: leading dimension too small");
     IPEPS_REQUIRE(ldc >= N, "gemm: leading dimension of C too small");
-    if (prec == IPEPS_TF32X3) ipeps::gemm_tf32x3(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    if (prec == IPEPS_TF32X3 || prec == IPEPS_TF32X3_ALL) ipeps::gemm_tf32x3(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     else if (prec == IPEPS_FP64) ipeps::gemm_f64(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     else throw ipeps::Error(IPEPS_ERR_ARG, "gemm: unknown precision");
     IPEPS_CUDA(cudaStreamSynchronize(s));
@@ -378,7 +378,8 @@ ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham h
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     IPEPS_REQUIRE(A_dev && ham && opts, "optimize: NULL argument");
     IPEPS_REQUIRE(opts->chi >= 1 && opts->ctm_maxit >= 1 && opts->history >= 0 && opts->maxiter >= 0 &&
-                      opts->krylov >= 1 && opts->restarts >= 1,
+                      opts->krylov >= 1 && opts->restarts >= 1 && opts->prec >= IPEPS_FP64 &&
+                      opts->prec <= IPEPS_TF32X3_ALL,
                   "optimize: bad options");
     IPEPS_REQUIRE(ham->impl.d == c.d, "optimize: Hamiltonian has a different d");
     check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");

@@ -32,12 +32,16 @@
 namespace ipeps {
 
 double sv_cutoff(Prec prec) {
-  if (prec == Prec::FP64) return kSvCutoff;
-  static const double c = [] {
+  // the split mode's projector SVD sees an FP64 four-corner product
+  static const double c64 = [] {
+    const char *e = std::getenv("IPEPS_SV_CUTOFF_FP64");
+    return e ? std::atof(e) : kSvCutoff;
+  }();
+  static const double c3 = [] {
     const char *e = std::getenv("IPEPS_SV_CUTOFF_TF32X3");
     return e ? std::atof(e) : 1e-7;
   }();
-  return c;
+  return prec == Prec::TF32X3_ALL ? c3 : c64;
 }
 
 namespace {
@@ -161,14 +165,21 @@ void left_move(Tape &t, const Cell &c, int chi, StateVars &sv, int r) {
       int Qll = corner_ul(t, E(C4, x, y + 1), E(T4, x, y + 1), E(T3, x, y + 1), Av(3, x, y + 1));
       int R1 = t_contract(t, Qul, "ab", Qur, "bc", "ac");
       int R2 = t_contract(t, Qlr, "ab", Qll, "bc", "ac");
+      // the four-corner product squares the dynamic range of the half systems:
+      // its small singular directions decide the projectors and sit below the
+      // 3xTF32 noise floor of |R2||R1|, so the split mode forms it (and the
+      // projector products) in FP64
+      const Prec keep = t.prec;
+      if (keep != Prec::TF32X3_ALL) t.prec = Prec::FP64;
       int M = t_contract(t, R2, "ab", R1, "bc", "ac");
       int N = int(t.val(M).d[0]);
       int U, S, V;
       t.vkey = (r * 64 + x) * 64 + y;
       t_svd(t, M, std::min(chi, N), &U, &S, &V);
-      int fs = t_inv_sqrt_cut(t, S, sv_cutoff(t.prec));
+      int fs = t_inv_sqrt_cut(t, S, sv_cutoff(keep));
       Pup[x * Ly + y] = t_scale_cols(t, t_contract(t, R2, "ba", U, "bk", "ak"), fs);
       Pdn[x * Ly + y] = t_scale_cols(t, t_contract(t, R1, "ab", V, "bk", "ak"), fs);
+      t.prec = keep;
     }
   // absorb column x into the left boundary of column x+1 (all columns)
   std::vector<std::tuple<int, int, int, int>> upd;  // (name, x, y, var) in frame r
@@ -294,12 +305,17 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
               cudaStream_t s) {
   const Cell &c = e.cell;
   const int nmat = 4 * c.nsites();
-  e.prec = prec;
   if (!e.have_spectra) corner_spectra(e, s);
   DBuf prev(size_t(nmat) * e.chi, s);
   double change = INFINITY;
+  // split precision: 3xTF32 iterations while the change is above the split
+  // floor and still improving, then (TF32X3) FP64 iterations down to tol
+  Prec phase = prec;
+  double best = INFINITY;
+  int since_best = 0;
   int it = 0;
   for (it = 1; it <= maxit; ++it) {
+    const Prec prec = phase;
     IPEPS_CUDA(cudaMemcpyAsync(prev.p, e.spectra.p, nmat * e.chi * sizeof(double),
                                cudaMemcpyDeviceToDevice, s));
     {
@@ -360,7 +376,12 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
     change = spectra_change(prev.p, e.spectra.p, nmat, e.chi, s);
     if (!std::isfinite(change)) throw Error(IPEPS_ERR_NONFINITE, "CTMRG produced non-finite values");
     if (change < tol && it >= 2) break;
+    if (change < 0.7 * best) { best = change; since_best = 0; }
+    else ++since_best;
+    if (phase == Prec::TF32X3 && (change < kSplitSwitch || since_best >= 10)) phase = Prec::FP64;
+    if (phase == Prec::TF32X3_ALL && since_best >= 10) break;  // at the noise floor
   }
+  e.prec = phase;
   if (it > maxit) it = maxit;
   if (err) *err = change;
   return it;

@@ -95,7 +95,7 @@ void contract(const Ten &A, const std::string &la, const Ten &B, const std::stri
     Cp = Cb.p;
   }
   double ga = direct ? alpha : 1.0, gb = direct ? beta : 0.0;
-  if (prec == Prec::TF32X3 && tc_worthwhile(m, n, k)) gemm_tf32x3(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
+  if (prec != Prec::FP64 && tc_worthwhile(m, n, k)) gemm_tf32x3(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
   else gemm_f64(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
   if (!direct) permute(Cp, dims_of(FA + FB), perm_to(FA + FB, lc), C.p, s, alpha, beta);
 }

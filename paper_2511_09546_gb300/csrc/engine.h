@@ -21,7 +21,7 @@
 
 namespace ipeps {
 
-enum class Prec { FP64 = 0, TF32X3 = 1 };
+enum class Prec { FP64 = 0, TF32X3 = 1, TF32X3_ALL = 2 };
 
 struct Ten {
   double *p = nullptr;

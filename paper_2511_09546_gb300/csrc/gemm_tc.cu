@@ -14,7 +14,7 @@
 // that grows linearly in K/8 and is biased; at K = 8192 that error is as large
 // as dropping the lo terms altogether.  The kernel therefore accumulates only
 // `chunk` K slices in TMEM, then adds the chunk's partial sums into a
-// compensated (two-sum) FP32 pair per output, also kept in TMEM, so the
+// compensated (two-sum) FP32 pair per output held in registers, so the
 // truncation bias no longer builds up across chunks.  Two TMEM accumulators
 // alternate, so the MMAs of one chunk overlap the flush of the previous one.
 //
@@ -23,8 +23,9 @@
 //     32 (w % 4) .. +31 (its rows) and columns 64 (w / 4) .. +63;
 //   * lane 0 of warp 8 streams 32-wide K slices of A' and B' with TMA (128-byte
 //     swizzle) into a ring of shared-memory stages guarded by mbarriers; warp 8
-//     also owns the TMEM allocation: two accumulators, then the hi and lo
-//     halves of the compensated sums (4 x 128 = 512 columns);
+//     also owns the TMEM allocation (two accumulators, 2 x 128 columns);
+//   * pairs of CTAs along N form a cluster and multicast the A slice they
+//     share, so each CTA reads half of it from L2;
 //   * lane 0 of warp 9 issues tcgen05.mma (M = 128, N = 128, K = 8, four per
 //     slice), releases each stage with tcgen05.commit and signals each
 //     finished chunk on the accumulator's mbarrier.
@@ -55,6 +56,7 @@ constexpr int STAGES = 6;        // shared-memory ring: 6 x 32 KB
 constexpr int FLUSH_WARPS = 8;   // warps 0-7
 constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
 constexpr int THREADS = 32 * (FLUSH_WARPS + 2);
+constexpr int TMEM_COLS = 4 * BN;  // two accumulators, the lo halves of the compensated sums, unused
 constexpr int WCOLS = BN / 2;    // accumulator columns per flush warp
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
@@ -157,15 +159,50 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// TMA load delivered to the same shared-memory offset (and mbarrier) of every CTA in mask
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                               uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
+      : "memory");
+}
+
+// completion of this CTA's MMAs, arrived on the mbarrier at the same offset in every CTA of mask
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
+// CL = CTAs per cluster along N.  With CL = 2 the two CTAs of a cluster share
+// the rows m0..m0+127 of A': each loads half of the A slice and multicasts it
+// to both, which halves the A traffic out of L2; a stage is refilled only
+// after the MMAs of both CTAs released it (empty barriers count CL arrivals).
+template <int CL, bool COMP>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int64_t M, int64_t N, int nk, int chunk, double alpha, double beta,
                    double *__restrict__ C, int64_t ldc, int *err) {
   constexpr uint32_t A_BYTES = BM * BKT * 4, B_BYTES = BN * BKT * 4;
+  constexpr uint16_t MASK = uint16_t((1u << CL) - 1);
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned ring of stages: [A stage | B stage] x STAGES
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -174,11 +211,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int nchunks = (nk + chunk - 1) / chunk;
+  const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
+      mbar_init(&empty[s], CL);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -189,12 +227,13 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == PRODUCER_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                 "r"(uint32_t(4 * BN))
+                 "r"(uint32_t(TMEM_COLS))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (CL > 1) cluster_sync();  // peers' barriers are initialised before any multicast reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
@@ -206,7 +245,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!mbar_wait(&empty[s], ((kt / STAGES) & 1) ^ 1, err)) break;
         uint8_t *sa = base + size_t(s) * (A_BYTES + B_BYTES);
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        tma_load_2d(sa, &mapA, &full[s], kt * BKT, m0);
+        if (CL == 1) {
+          tma_load_2d(sa, &mapA, &full[s], kt * BKT, m0);
+        } else {
+          // rows m0 + crank*BM/CL .. +BM/CL of the slice, to this offset in every CTA of the cluster
+          tma_load_2d_mc(sa + crank * (A_BYTES / CL), &mapA, &full[s], kt * BKT, m0 + int(crank) * (BM / CL),
+                         MASK);
+        }
         tma_load_2d(sa + A_BYTES, &mapB, &full[s], kt * BKT, n0);
         issued = kt + 1;
       }
@@ -234,73 +279,74 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int ks = 0; ks < BKT / 8; ++ks)  // 8 TF32 = 32 bytes per MMA: +2 in the address field
             mma_tf32(acc, ad + 2 * ks, bd + 2 * ks, idesc, (kt != k_first || ks != 0) ? 1u : 0u);
-          mma_commit(&empty[s]);
+          if (CL == 1) mma_commit(&empty[s]);
+          else mma_commit_mc(&empty[s], MASK);
         }
         if (ok) mma_commit(&acc_full[b]);
       }
     }
   } else {
-    // ---- flush warps: chunk partials (TMEM, FP32) -> compensated pair (hi, lo), also in TMEM
+    // ---- flush warps: chunk partials (TMEM, FP32) -> running sums hi (registers)
+    // and, when COMP, the two-sum error terms lo (TMEM columns 2 BN ..)
     const uint32_t lanes = uint32_t((warp & 3) * 32) << 16, cw = uint32_t((warp >> 2) * WCOLS);
-    const uint32_t t_acc = tmem + lanes + cw, t_hi = tmem + lanes + 2 * BN + cw, t_lo = t_hi + BN;
+    const uint32_t t_acc = tmem + lanes + cw, t_lo = tmem + lanes + 2 * BN + cw;
+    float hi[WCOLS];
+#pragma unroll
+    for (int j = 0; j < WCOLS; ++j) hi[j] = 0.0f;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1, use = c >> 1;
       ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[b], use & 1, err) ? 1 : 0) != 0;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
+#pragma unroll
       for (int q = 0; q < WCOLS / 16; ++q) {
-        uint32_t v[16], h[16], l[16];
+        uint32_t v[16], l[16];
         tmem_ld16_issue(t_acc + uint32_t(b * BN + q * 16), v);
-        if (c > 0) {
-          tmem_ld16_issue(t_hi + uint32_t(q * 16), h);
-          tmem_ld16_issue(t_lo + uint32_t(q * 16), l);
-          tmem_ld_wait(v);
-          tmem_ld_wait(h);
-          tmem_ld_wait(l);
+        if (COMP && c > 0) tmem_ld16_issue(t_lo + uint32_t(q * 16), l);
+        tmem_ld_wait(v);
+        if (q == WCOLS / 16 - 1) {
+          // the accumulator is in registers: hand it back to the MMA warp before the last adds
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[b]);
+        }
+        if (COMP) {
+          if (c > 0) tmem_ld_wait(l);
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             // two-sum: hi + x = sum + e exactly
-            const float x = __uint_as_float(v[j]), hv = __uint_as_float(h[j]);
+            const float x = __uint_as_float(v[j]), hv = hi[q * 16 + j];
             const float sum = hv + x, bv = sum - hv;
             const float e = (hv - (sum - bv)) + (x - bv);
-            h[j] = __float_as_uint(sum);
-            l[j] = __float_as_uint(__uint_as_float(l[j]) + e);
+            hi[q * 16 + j] = sum;
+            l[j] = __float_as_uint(c > 0 ? __uint_as_float(l[j]) + e : e);
           }
+          tmem_st16(t_lo + uint32_t(q * 16), l);
         } else {
-          tmem_ld_wait(v);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            h[j] = v[j];
-            l[j] = 0u;
-          }
+          for (int j = 0; j < 16; ++j) hi[q * 16 + j] += __uint_as_float(v[j]);
         }
-        tmem_st16(t_hi + uint32_t(q * 16), h);
-        tmem_st16(t_lo + uint32_t(q * 16), l);
       }
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acc_empty[b]);
+      if (COMP) asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
     if (ok) {
       const int64_t row = m0 + (warp & 3) * 32 + lane;
       const int64_t col0 = n0 + (warp >> 2) * WCOLS;
-#pragma unroll 1
+#pragma unroll
       for (int q = 0; q < WCOLS / 16; ++q) {
-        uint32_t h[16], l[16];
-        tmem_ld16_issue(t_hi + uint32_t(q * 16), h);
-        tmem_ld16_issue(t_lo + uint32_t(q * 16), l);
-        tmem_ld_wait(h);
-        tmem_ld_wait(l);
+        uint32_t l[16];
+        if (COMP) {
+          tmem_ld16_issue(t_lo + uint32_t(q * 16), l);
+          tmem_ld_wait(l);
+        }
         if (row < M) {
           double *crow = C + row * ldc + col0 + q * 16;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             if (col0 + q * 16 + j < N) {
-              const double out = alpha * (double(__uint_as_float(h[j])) + double(__uint_as_float(l[j])));
-              crow[j] = (beta == 0.0) ? out : out + beta * crow[j];
+              const double sum = double(hi[q * 16 + j]) + (COMP ? double(__uint_as_float(l[j])) : 0.0);
+              crow[j] = (beta == 0.0) ? alpha * sum : alpha * sum + beta * crow[j];
             }
           }
         }
@@ -314,9 +360,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write its shared memory
   if (warp == PRODUCER_WARP) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(4 * BN))
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TMEM_COLS))
                  : "memory");
   }
 }
@@ -396,25 +443,56 @@ int *error_word(cudaStream_t s) {
   return w;
 }
 
-void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, int nk, int chunk, double alpha,
-            double beta, double *C, int64_t ldc, int *err, cudaStream_t s) {
+template <int CL, bool COMP>
+void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, int64_t Np, int nk, int chunk,
+            double alpha, double beta, double *C, int64_t ldc, int *err, cudaStream_t s) {
   constexpr size_t smem = size_t(STAGES) * (BM + BN) * BKT * 4 + 1024;
   static bool attr = false;
   if (!attr) {
-    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<CL, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     attr = true;
   }
-  dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM));
-  tc_gemm_kernel<<<grd, THREADS, smem, s>>>(ma, mb, M, N, nk, chunk, alpha, beta, C, ldc, err);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(Np / BN), unsigned((M + BM - 1) / BM));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  IPEPS_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<CL, COMP>, ma, mb, M, N, nk, chunk, alpha, beta,
+                                C, ldc, err));
   count_launch();
   check_launch("tc_gemm");
+}
+
+bool compensated() {
+  // two-sum compensation of the sum over chunks (default on)
+  static bool c = [] {
+    const char *e = std::getenv("IPEPS_TC_COMP");
+    return !(e && std::atoi(e) == 0);
+  }();
+  return c;
+}
+
+int cluster_n() {
+  // CTAs per cluster along N (1 or 2): TMA multicast of the shared A slice
+  static int c = [] {
+    const char *e = std::getenv("IPEPS_TC_CLUSTER");
+    return (e && std::atoi(e) == 2) ? 2 : 1;
+  }();
+  return c;
 }
 
 int chunk_slices() {
   // K slices (32 TF32 elements of the tripled K) per TMEM accumulation chunk
   static int c = [] {
     const char *e = std::getenv("IPEPS_TC_CHUNK");
-    int v = e ? std::atoi(e) : 4;
+    int v = e ? std::atoi(e) : 8;
     return v < 1 ? 1 : v;
   }();
   return c;
@@ -431,7 +509,8 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
   }
   IPEPS_REQUIRE((M + BM - 1) / BM <= 65535, "tc_gemm: M too large");
   const int64_t Kp = (K + BKT - 1) / BKT * BKT, Kt = 3 * Kp;
-  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + BN - 1) / BN * BN;
+  const int cl = cluster_n();
+  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + cl * BN - 1) / (cl * BN) * (cl * BN);
   IPEPS_REQUIRE(Kt / BKT <= 2147483647 && Kp / 32 <= 2147483647, "tc_gemm: K too large");
   float *Ap = static_cast<float *>(dev_alloc(size_t(Mp) * Kt * sizeof(float), s));
   float *Bp = static_cast<float *>(dev_alloc(size_t(Np) * Kt * sizeof(float), s));
@@ -445,12 +524,17 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
     count_launch(2);
     check_launch("tc_pack");
   }
-  const CUtensorMap ma = make_map(Ap, Mp, Kt, BM);
+  const CUtensorMap ma = make_map(Ap, Mp, Kt, BM / cl);
   const CUtensorMap mb = make_map(Bp, Np, Kt, BN);
   int *err = error_word(s);
   {
     ProfScope prof("tc_gemm", s, 2.0 * M * N * K, 4.0 * (Mp + Np) * Kt + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
-    launch(ma, mb, M, N, int(Kt / BKT), chunk_slices(), alpha, beta, C, ldc, err, s);
+    const int nk = int(Kt / BKT), ch = chunk_slices();
+    const bool comp = compensated();
+    if (cl == 2 && comp) launch<2, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (cl == 2) launch<2, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (comp) launch<1, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else launch<1, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
   }
   int h = 0;
   IPEPS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -18,11 +18,13 @@ namespace ipeps {
 // Boundary tensor names; legs of a corner are (prev, next), of an edge
 // (prev, ket, bra, next), running clockwise C1 T1 C2 T2 C3 T3 C4 T4.
 enum Name { C1 = 0, C2, C3, C4, T1, T2, T3, T4 };
+constexpr double kSplitSwitch = 1e-6;  // split mode: spectra change at which FP64 takes over
 constexpr double kSvCutoff = 1e-12;  // relative cut of the projector spectrum (FP64 GEMMs)
 // Relative cut of the projector spectrum for the precision the enlarged corners
 // were contracted in: singular values of the four-corner product below the
 // GEMM error floor carry no information, and S^-1/2 would amplify that noise
-// into the projectors.  IPEPS_SV_CUTOFF_TF32X3 overrides the split-precision cut.
+// into the projectors.  IPEPS_SV_CUTOFF_FP64 / IPEPS_SV_CUTOFF_TF32X3 override
+// the two cuts (1e-12 and 1e-7).
 double sv_cutoff(Prec prec);
 
 struct Cell {
@@ -52,7 +54,7 @@ struct EnvImpl {
   DBuf spectra;          // last corner spectra (4 * Lx * Ly * chi)
   bool have_spectra = false;
   std::map<int, DBuf> svd_cache;  // warm starts of the projector SVDs
-  Prec prec = Prec::FP64;         // GEMM precision of the last CTMRG run (reused by the adjoint)
+  Prec prec = Prec::FP64;         // precision of the last CTMRG iterations (reused by the adjoint)
   cudaStream_t s = nullptr;
   int64_t csize() const { return int64_t(chi) * chi; }
   int64_t esize() const { return int64_t(chi) * cell.D * cell.D * chi; }
