@@ -1,6 +1,8 @@
 // FP64 GEMM on the CUDA cores (DFMA).  GB300's FP64 rate is about 2 DFMA per
 // clock per SM, so a 64x64 register-blocked tile is compute bound at every
-// shape the CTMRG produces; the kernel favours simplicity and exact FP64.
+// shape the CTMRG produces; the kernel favours simplicity and exact FP64, and
+// the dispatcher's job is to keep every SM's FP64 pipe busy (split K whenever
+// there are fewer output tiles than SMs).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -193,9 +195,11 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
     check_launch("dgemm perout");
     return;
   }
-  if (batch == 1 && tiles < sms && K >= 1024) {
-    // few output tiles and a long K: split K over the idle SMs, then reduce
-    int64_t S = std::min<int64_t>((2 * sms + tiles - 1) / tiles, (K + 511) / 512);
+  if (batch == 1 && tiles < sms && K >= 32) {
+    // fewer output tiles than SMs: split K so that every SM gets a slice (the
+    // FP64 pipe, ~2 DFMA per clock per SM, is the limit, not memory), slices of
+    // at least 16, then reduce
+    int64_t S = std::min<int64_t>((sms + tiles - 1) / tiles, K / 16);
     S = std::min<int64_t>(S, 512);
     if (S >= 2) {
       int64_t kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
