@@ -50,14 +50,15 @@ namespace ipeps {
 namespace {
 
 constexpr int BM = 128;          // rows per tile (TMEM lanes)
-constexpr int BN = 128;          // columns per tile (TMEM columns per accumulator)
 constexpr int BKT = 32;          // TF32 elements per K slice = 128 bytes (one swizzle row)
-constexpr int STAGES = 6;        // shared-memory ring: 6 x 32 KB
-constexpr int FLUSH_WARPS = 8;   // warps 0-7
-constexpr int PRODUCER_WARP = 8, MMA_WARP = 9;
-constexpr int THREADS = 32 * (FLUSH_WARPS + 2);
-constexpr int TMEM_COLS = 4 * BN;  // two accumulators, the lo halves of the compensated sums, unused
-constexpr int WCOLS = BN / 2;    // accumulator columns per flush warp
+constexpr int RING_BYTES = 204800;  // shared-memory ring: 6 x 32 KB (BN 128), 5 x 40 KB (BN 192)
+constexpr int GROUP_M = 8;       // CTA raster: 8 tile rows per group share the B' tiles in L2
+constexpr int WCOLS = 64;        // accumulator columns per flush warp
+// warps 0 .. 4 BN/64 - 1 flush (lane quarter w % 4, columns 64 (w / 4) ..),
+// then one producer warp and one MMA warp
+template <int BN> __host__ __device__ constexpr int flush_warps() { return 4 * (BN / WCOLS); }
+template <int BN> __host__ __device__ constexpr int threads() { return 32 * (flush_warps<BN>() + 2); }
+constexpr int TMEM_COLS = 512;   // BN 256: two accumulators; BN 128: two accumulators, lo, spare
 constexpr long long kWaitCycles = 4000000000ll;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -196,20 +197,32 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // the rows m0..m0+127 of A': each loads half of the A slice and multicasts it
 // to both, which halves the A traffic out of L2; a stage is refilled only
 // after the MMAs of both CTAs released it (empty barriers count CL arrivals).
-template <int CL, bool COMP>
-__global__ void __launch_bounds__(THREADS, 1)
+template <int BN, int CL, bool COMP>
+__global__ void __launch_bounds__(threads<BN>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int64_t M, int64_t N, int nk, int chunk, double alpha, double beta,
                    double *__restrict__ C, int64_t ldc, int *err) {
   constexpr uint32_t A_BYTES = BM * BKT * 4, B_BYTES = BN * BKT * 4;
+  constexpr int STAGES = RING_BYTES / int(A_BYTES + B_BYTES);
+  constexpr int FLUSH_WARPS = flush_warps<BN>(), PRODUCER_WARP = FLUSH_WARPS, MMA_WARP = FLUSH_WARPS + 1;
   constexpr uint16_t MASK = uint16_t((1u << CL) - 1);
+  static_assert(!COMP || 4 * BN <= TMEM_COLS, "the lo halves need TMEM columns 2 BN .. 3 BN");
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned ring of stages: [A stage | B stage] x STAGES
   uint8_t *base = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  int mt = blockIdx.y, ntile = blockIdx.x;
+  if (CL == 1) {
+    // grouped raster: consecutive CTAs walk GROUP_M tile rows column by column
+    const int nt = gridDim.x, mtiles = gridDim.y;
+    const int id = blockIdx.y * nt + blockIdx.x, per = GROUP_M * nt;
+    const int first = (id / per) * GROUP_M, rows = min(GROUP_M, mtiles - first);
+    mt = first + (id % per) % rows;
+    ntile = (id % per) / rows;
+  }
+  const int m0 = mt * BM, n0 = ntile * BN;
   const int nchunks = (nk + chunk - 1) / chunk;
   const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
 
@@ -350,6 +363,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
           }
         }
+        // one 16-column group of C traffic at a time: keeps the beta*C loads
+        // from being hoisted next to the live running sums
+        asm volatile("" ::: "memory");
       }
     }
   }
@@ -443,18 +459,19 @@ int *error_word(cudaStream_t s) {
   return w;
 }
 
-template <int CL, bool COMP>
+template <int BN, int CL, bool COMP>
 void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, int64_t Np, int nk, int chunk,
             double alpha, double beta, double *C, int64_t ldc, int *err, cudaStream_t s) {
-  constexpr size_t smem = size_t(STAGES) * (BM + BN) * BKT * 4 + 1024;
+  constexpr size_t stage = size_t(BM + BN) * BKT * 4;
+  constexpr size_t smem = (RING_BYTES / stage) * stage + 1024;
   static bool attr = false;
   if (!attr) {
-    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<CL, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, CL, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(Np / BN), unsigned((M + BM - 1) / BM));
-  cfg.blockDim = dim3(THREADS);
+  cfg.blockDim = dim3(threads<BN>());
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -464,7 +481,7 @@ void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  IPEPS_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<CL, COMP>, ma, mb, M, N, nk, chunk, alpha, beta,
+  IPEPS_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, CL, COMP>, ma, mb, M, N, nk, chunk, alpha, beta,
                                 C, ldc, err));
   count_launch();
   check_launch("tc_gemm");
@@ -510,7 +527,10 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
   IPEPS_REQUIRE((M + BM - 1) / BM <= 65535, "tc_gemm: M too large");
   const int64_t Kp = (K + BKT - 1) / BKT * BKT, Kt = 3 * Kp;
   const int cl = cluster_n();
-  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + cl * BN - 1) / (cl * BN) * (cl * BN);
+  // wide outputs: 192-column tiles (less shared-memory traffic per MMA),
+  // plain FP32 sum over chunks; narrow outputs: 128-column tiles, compensated
+  const int bn = N > 128 ? 192 : 128;
+  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + cl * bn - 1) / (cl * bn) * (cl * bn);
   IPEPS_REQUIRE(Kt / BKT <= 2147483647 && Kp / 32 <= 2147483647, "tc_gemm: K too large");
   float *Ap = static_cast<float *>(dev_alloc(size_t(Mp) * Kt * sizeof(float), s));
   float *Bp = static_cast<float *>(dev_alloc(size_t(Np) * Kt * sizeof(float), s));
@@ -525,16 +545,18 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
     check_launch("tc_pack");
   }
   const CUtensorMap ma = make_map(Ap, Mp, Kt, BM / cl);
-  const CUtensorMap mb = make_map(Bp, Np, Kt, BN);
+  const CUtensorMap mb = make_map(Bp, Np, Kt, bn);
   int *err = error_word(s);
   {
     ProfScope prof("tc_gemm", s, 2.0 * M * N * K, 4.0 * (Mp + Np) * Kt + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
     const int nk = int(Kt / BKT), ch = chunk_slices();
     const bool comp = compensated();
-    if (cl == 2 && comp) launch<2, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else if (cl == 2) launch<2, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else if (comp) launch<1, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else launch<1, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    if (bn == 192 && cl == 2) launch<192, 2, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (bn == 192) launch<192, 1, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (cl == 2 && comp) launch<128, 2, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (cl == 2) launch<128, 2, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (comp) launch<128, 1, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else launch<128, 1, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
   }
   int h = 0;
   IPEPS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
