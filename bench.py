@@ -110,7 +110,7 @@ def run_ours(args, rank, world, local):
     cell = w["gen"]()
     A_host = ipeps.cell_tensor(cell)
     ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
-    prec = ipeps.TF32X3 if args.prec == "tf32x3" else ipeps.FP64
+    prec = _prec(ipeps, args.prec)
     K, W = args.steps, args.warmup
     opts = ipeps.default_opts(chi=w["chi"], maxiter=W + K, precondition=1, ctm_tol=1e-10, ctm_maxit=120,
                               prec=prec, gtol=0.0)
@@ -246,7 +246,7 @@ def run_passes(args):
     w = inputs.WORKLOADS[args.workload]
     A0 = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
     ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
-    prec = ipeps.TF32X3 if args.prec == "tf32x3" else ipeps.FP64
+    prec = _prec(ipeps, args.prec)
     gen = torch.Generator(device="cpu").manual_seed(1)
     env, _, _ = ipeps.ctmrg(A0, w["chi"], tol=1e-10, maxit=200, prec=prec, allow_unconverged=True)
     lat = []
@@ -294,6 +294,66 @@ def oracle_sample(workload, n_ctm=1):
     return dt, torch.get_num_threads()
 
 
+def _prec(ipeps, name):
+    return {"fp64": ipeps.FP64, "tf32x3": ipeps.TF32X3, "tf32x3_all": ipeps.TF32X3_ALL}[name]
+
+
+def run_ctmrg(args):
+    """--mode ctmrg: CTMRG throughput.  W warm-up iterations (cold start and chi
+    growth), then K timed iterations, each one full CTMRG iteration (4 directional
+    moves, Lx*Ly projector pairs each) warm-started from the previous one; prints
+    one JSON line with iterations/s, moves/s and TFLOP/s (library profiler)."""
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import inputs, ipeps
+
+    w = inputs.WORKLOADS[args.workload]
+    A = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
+    prec = _prec(ipeps, args.prec)
+    free0 = torch.cuda.mem_get_info()[0]
+    env = None
+    for _ in range(args.warmup):
+        env, _, _ = ipeps.ctmrg(A, w["chi"], tol=1e-30, maxit=1, prec=prec, env=env, allow_unconverged=True)
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info()[0]
+    ipeps.profile(True)
+    lat = []
+    for _ in range(args.steps):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        env, _, err = ipeps.ctmrg(A, w["chi"], tol=1e-30, maxit=1, prec=prec, env=env, allow_unconverged=True)
+        t1.record()
+        torch.cuda.synchronize()
+        lat.append(t0.elapsed_time(t1))
+    st = ipeps.profile_stats()
+    ipeps.profile(False)
+    tot_ms = sum(lat)
+    peaks = _peaks()
+    tf32_peak = peaks.get("bf16_tflops", 1885.7) / 2.0
+    n = w["chi"] * w["D"] ** 2
+    pairs = 4 * w["Lx"] * w["Ly"]
+    model = pairs * 3 * 2.0 * n ** 3  # the S3 products alone, 2 flop per MAC
+    flops = sum(v["flops"] for k, v in st.items() if k in ("dgemm", "tc_gemm"))
+    gm = st.get("tc_gemm", {"ms": 0.0, "flops": 0.0, "count": 0})
+    rec = {"mode": "ctmrg", "workload": args.workload, "precision": args.prec, "iterations": len(lat),
+           "ms_per_iteration": tot_ms / max(1, len(lat)),
+           "ctmrg_iterations_per_s": 1e3 * len(lat) / tot_ms, "moves_per_s": 4e3 * len(lat) / tot_ms,
+           "gemm_tflops": flops / (tot_ms * 1e-3) / 1e12,
+           "s3_model_tflop_per_iteration": model / 1e12,
+           "tc_gemm": {"share": gm["ms"] / tot_ms, "launches": gm["count"],
+                       "logical_tflops": gm["flops"] / max(1e-9, gm["ms"] * 1e-3) / 1e12,
+                       "issued_frac_of_tf32_peak": 3 * gm["flops"] / max(1e-9, gm["ms"] * 1e-3) / 1e12 / tf32_peak},
+           "last_change": err, "device_bytes_after_warmup": int(free0 - free1),
+           "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 2),
+                           "tflops": round(v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12, 3)}
+                       for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
+    print(json.dumps(rec), flush=True)
+
+
 def run_gemm(args):
     """--mode gemm: the 3xTF32 tcgen05 GEMM on n x n x n FP64 operands, timed per
     kernel class with CUDA events (W warm-up calls, K timed calls)."""
@@ -339,10 +399,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3"])
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "tf32x3_all"])
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass", "gemm"])
+    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass", "gemm", "ctmrg"])
     ap.add_argument("--gemm-n", type=int, default=8192)
     args = ap.parse_args()
     rank, world, local = _dist()
@@ -351,6 +411,9 @@ def main():
         return
     if args.mode == "gemm":
         run_gemm(args)
+        return
+    if args.mode == "ctmrg":
+        run_ctmrg(args)
         return
     if args.impl == "reference":
         if rank != 0:

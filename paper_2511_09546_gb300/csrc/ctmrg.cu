@@ -134,6 +134,9 @@ int corner_ul(Tape &t, int c1, int t1, int t4, int a) {
   int X2 = t_contract(t, t4, "fgha", X1, "acde", "fghcde");   // [T4.p, l, l', u, u', T1.n]
   int X3 = t_contract(t, X2, "fghcde", a, "scgjk", "fhdesjk"); // ket A on (u, l)
   int X4 = t_contract(t, X3, "fhdesjk", a, "sdhmn", "fjmekn"); // bra A on (s, u', l')
+  t.release(X1);
+  t.release(X2);
+  t.release(X3);
   const auto &d = t.val(X4).d;
   return t_reshape(t, X4, {d[0] * d[1] * d[2], d[3] * d[4] * d[5]});
 }
@@ -165,6 +168,7 @@ void left_move(Tape &t, const Cell &c, int chi, StateVars &sv, int r) {
       int Qll = corner_ul(t, E(C4, x, y + 1), E(T4, x, y + 1), E(T3, x, y + 1), Av(3, x, y + 1));
       int R1 = t_contract(t, Qul, "ab", Qur, "bc", "ac");
       int R2 = t_contract(t, Qlr, "ab", Qll, "bc", "ac");
+      for (int q : {Qul, Qur, Qlr, Qll}) t.release(q);
       // the four-corner product squares the dynamic range of the half systems:
       // its small singular directions decide the projectors and sit below the
       // 3xTF32 noise floor of |R2||R1|, so the split mode forms it (and the
@@ -176,10 +180,13 @@ void left_move(Tape &t, const Cell &c, int chi, StateVars &sv, int r) {
       int U, S, V;
       t.vkey = (r * 64 + x) * 64 + y;
       t_svd(t, M, std::min(chi, N), &U, &S, &V);
+      t.release(M);
       int fs = t_inv_sqrt_cut(t, S, sv_cutoff(keep));
       Pup[x * Ly + y] = t_scale_cols(t, t_contract(t, R2, "ba", U, "bk", "ak"), fs);
       Pdn[x * Ly + y] = t_scale_cols(t, t_contract(t, R1, "ab", V, "bk", "ak"), fs);
       t.prec = keep;
+      t.release(R1);
+      t.release(R2);
     }
   // absorb column x into the left boundary of column x+1 (all columns)
   std::vector<std::tuple<int, int, int, int>> upd;  // (name, x, y, var) in frame r
@@ -190,12 +197,21 @@ void left_move(Tape &t, const Cell &c, int chi, StateVars &sv, int r) {
       const auto &dx = t.val(X).d;
       X = t_reshape(t, X, {dx[0] * dx[1] * dx[2], dx[3]});
       int c1 = t_contract(t, Pup[x * Ly + ym], "ak", X, "an", "kn");
-      int Y = t_contract(t, E(T4, x, y), "plqn", Av(0, x, y), "suldr", "pqnsudr");
-      Y = t_contract(t, Y, "pqnsudr", Av(0, x, y), "svqeg", "pdergnuv");  // [p,d,d',r,r',n,u,u']
-      const auto &dy = t.val(Y).d;
-      Y = t_reshape(t, Y, {dy[0] * dy[1] * dy[2], dy[3], dy[4], dy[5] * dy[6] * dy[7]});
-      int t4 = t_contract(t, Pup[x * Ly + y], "ak", Y, "arsb", "krsb");
-      t4 = t_contract(t, t4, "krsb", Pdn[x * Ly + ym], "bm", "krsm");
+      // T4' = Pup^T (T4 A Abar) Pdn with the projectors applied first, so no
+      // intermediate exceeds chi^2 D^4 d entries: Pup rows are (p, d, d'),
+      // Pdn rows are (n, u, u')
+      const int et4 = E(T4, x, y);
+      const auto dt = t.val(et4).d;  // [p, D, D, n]
+      const int pu = Pup[x * Ly + y], pd = Pdn[x * Ly + ym];
+      const int pu4 = t_reshape(t, pu, {dt[0], dt[1], dt[2], t.val(pu).d[1]});
+      const int pd4 = t_reshape(t, pd, {dt[3], dt[1], dt[2], t.val(pd).d[1]});
+      int W1 = t_contract(t, pu4, "pdek", et4, "plqn", "deklqn");
+      int W2 = t_contract(t, W1, "deklqn", Av(0, x, y), "suldr", "ekqnsur");  // ket A on (l, d)
+      t.release(W1);
+      int W3 = t_contract(t, W2, "ekqnsur", Av(0, x, y), "svqeg", "knurvg");  // bra A on (s, l', d')
+      t.release(W2);
+      int t4 = t_contract(t, W3, "knurvg", pd4, "nuvm", "krgm");
+      t.release(W3);
       int Z = t_contract(t, E(T3, x, y), "pden", E(C4, x, y), "nm", "pmde");
       const auto &dz = t.val(Z).d;
       Z = t_reshape(t, Z, {dz[0], dz[1] * dz[2] * dz[3]});

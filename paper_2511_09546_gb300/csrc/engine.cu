@@ -165,6 +165,12 @@ void Tape::clear() {
   vars.clear();
 }
 
+void Tape::release(int id) {
+  if (record) return;
+  while (vars[id].alias >= 0) id = vars[id].alias;
+  vars[id].own.release();
+}
+
 namespace {
 
 Ten gten(Tape &t, int id, double *g) { return Ten{g, t.val(id).d}; }
@@ -452,6 +458,17 @@ __global__ void colnorm_contig(const double *G, int64_t m, double *out) {
 
 // flip column j of U and V (row-major N x ncols, j < k) so that the entry of U
 // with the largest magnitude is positive
+// uniform [-1, 1) from a counter hash (splitmix64 finaliser) of (seed, index)
+__global__ void random_fill_kernel(double *p, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    uint64_t z = seed + uint64_t(i) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    p[i] = double(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
 __global__ void svd_sign_kernel(double *U, double *V, int64_t N, int64_t ncols) {
   int64_t j = blockIdx.x;
   __shared__ double bv[256];
@@ -624,9 +641,19 @@ void t_svd(Tape &t, int M, int k, int *U, int *S, int *V) {
     DBuf &vc = (*t.vcache)[t.vkey];
     const size_t csz = size_t(N * kb + kb);
     bool warm = vc.p != nullptr && vc.n == csz;
+    if (!warm && N > 1024) {
+      // cold start of a large cut: randomised range finder (random block, unit
+      // scales) instead of the full Jacobi SVD of an N x N matrix
+      vc = DBuf(csz, t.s);
+      random_fill_kernel<<<512, 256, 0, t.s>>>(vc.p, N * kb, 0x9E3779B97F4A7C15ull + uint64_t(t.vkey));
+      fill(vc.p + N * kb, kb, 1.0, t.s);
+      count_launch();
+      warm = true;
+    }
     DBuf Ub(size_t(N * kb), t.s), Sb(size_t(kb), t.s), Vb(size_t(N * kb), t.s);
     int its = 0;
-    bool ok = warm && svd_subspace(t.vp(M), N, k, int(kb), vc.p, Ub.p, Sb.p, Vb.p, t.s, &its);
+    bool ok = warm && svd_subspace(t.vp(M), N, k, int(kb), vc.p, Ub.p, Sb.p, Vb.p, t.s, &its,
+                                   t.prec == Prec::TF32X3_ALL);
     t.svd_iters += its;
     if (!ok) {
       if (std::getenv("IPEPS_DEBUG"))

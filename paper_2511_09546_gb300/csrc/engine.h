@@ -81,6 +81,10 @@ struct Tape {
   }
   void backward();      // replay adjoints (all nodes, reverse order)
   void clear();         // drop nodes and variables
+  // forward-only passes: free the storage behind id (and behind the variable a
+  // reshape view of it aliases); the caller uses none of them again.  A
+  // recording tape keeps every value for the backward pass, so this is a no-op.
+  void release(int id);
 };
 
 // ---- recorded primitives (return the new variable id)
@@ -111,7 +115,7 @@ void svd_full(const double *M, int64_t N, double *U, double *S, double *V, cudaS
 // U, V row-major N x k, S descending.  Returns false (nothing written to the
 // cache) when the block is numerically rank deficient; callers then use svd_full.
 bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, double *U, double *S,
-                  double *V, cudaStream_t s, int *iters);
+                  double *V, cudaStream_t s, int *iters, bool tc = false);
 // records the adjoint of the top-chi triplets computed from a kb-block
 void push_trunc_svd_node(Tape &t, int M, int U, int S, int V, int64_t N, int chi, int kb, DBuf &&Uk,
                          DBuf &&Sk, DBuf &&Vk);
