@@ -97,6 +97,22 @@ class Clocks:
         return out
 
 
+def replica_rate(local_ms, n_units, world):
+    """Whole-job rate of `world` independent replicas, each timing n_units units
+    in local_ms: (slowest rank's ms, world * n_units / slowest time in s).  The
+    max over ranks is an all-reduce on the process group's own device."""
+    import torch
+
+    t = torch.tensor([float(local_ms)], dtype=torch.float64)
+    if world > 1:
+        dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+        t = t.to(dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t = t.cpu()
+    slowest = float(t[0])
+    return slowest, (world * n_units / (slowest / 1000.0) if slowest > 0 else 0.0)
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -151,15 +167,8 @@ def run_ours(args, rank, world, local):
     clocks = state["clocks"].stop() if state["clocks"] else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
     timed = [i for i in range(W + 1, W + K + 1) if i in starts and i in ends]
     lat = [starts[i].elapsed_time(ends[i]) for i in timed]
-    total_ms = sum(lat)
-    t_local = np.array([total_ms], dtype=np.float64)
-    if world > 1:
-        tt = torch.tensor(t_local, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_local = tt.cpu().numpy()
-    total_ms = float(t_local[0])
     n_timed = len(timed)
-    value = world * n_timed / (total_ms / 1000.0) if total_ms > 0 else 0.0
+    total_ms, value = replica_rate(sum(lat), n_timed, world)
 
     # ---- end to end through the C ABI with host buffers (H2D + D2H inside)
     torch.cuda.synchronize()
