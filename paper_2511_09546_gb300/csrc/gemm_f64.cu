@@ -196,10 +196,11 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
     return;
   }
   if (batch == 1 && tiles < sms && K >= 32) {
-    // fewer output tiles than SMs: split K so that every SM gets a slice (the
-    // FP64 pipe, ~2 DFMA per clock per SM, is the limit, not memory), slices of
-    // at least 16, then reduce
-    int64_t S = std::min<int64_t>((sms + tiles - 1) / tiles, K / 16);
+    // fewer output tiles than SMs: split K so that the tiles x slices CTAs fill
+    // the SMs in one wave (the FP64 pipe, ~2 DFMA per clock per SM, is the
+    // limit, so a CTA more than the SM count doubles the time), slices of at
+    // least 16, then reduce
+    int64_t S = std::min<int64_t>(sms / tiles, K / 16);
     S = std::min<int64_t>(S, 512);
     if (S >= 2) {
       int64_t kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
