@@ -15,6 +15,14 @@ patch and the right half of site (x+1, y)'s patch; rho_v is rho_h of the
 picture rotated counter-clockwise (the lower site becomes the right site);
 rho_1 is the single-site density matrix of the 3x3 patch.
 
+Next-nearest-neighbour terms (J1-J2 model, the 'h_nnn' of the survey's S0 and
+the 2x2 plaquette of S7): a Hamiltonian with 'd1' / 'd2' operators adds, per
+site (x, y), Tr(rho_d1 d1)/Tr rho_d1 for the diagonal (x, y)-(x+1, y+1) and
+Tr(rho_d2 d2)/Tr rho_d2 for the anti-diagonal (x+1, y)-(x, y+1).  Both come
+from the ring of the four enlarged corners of the 2x2 plaquette with upper-left
+site (x, y) (the ring the projectors are built from), with the physical legs
+of the two sites of the pair left open.
+
 Parity pins: D=1 product states (closed forms), the Ising PEPS (Onsager),
 infinite cylinders (tests/test_oracle_ctmrg.py).
 """
@@ -23,7 +31,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .ctmrg import DT, rotate
+from .ctmrg import DT, corner_ul, rot_A, rotate
 
 
 def _env_left(C1, T1, T4, T3, C4):
@@ -69,6 +77,39 @@ def rho_1(A, env, x, y):
     return torch.einsum("crwest,crwe->st", L, RC)
 
 
+def corner_open(C1, T1, T4, A):
+    """Upper-left enlarged corner with the site's ket and bra physical legs open:
+    [(T4.prev, d, d'), (T1.next, r, r'), s, s']."""
+    X = torch.einsum("ab,bcde->acde", C1, T1)            # [C1.p, u, u', T1.n]
+    X = torch.einsum("fgha,acde->fghcde", T4, X)         # [T4.p, l, l', u, u', T1.n]
+    X = torch.einsum("fghcde,scgjk->fhdesjk", X, A)      # ket A on (u, l)
+    X = torch.einsum("fhdesjk,tdhmn->fjmeknst", X, A)    # bra A on (u', l'), physical t open
+    p, D1, _, n, D2, _, d, _ = X.shape
+    return X.reshape(p * D1 * D1, n * D2 * D2, d, d)
+
+
+def rho_diag(Lx, Ly, A, env, x, y, which):
+    """Two-site density matrix rho[s1, s1', s2, s2'] of the plaquette with
+    upper-left site (x, y): which=1 pairs (x, y) with (x+1, y+1), which=2 pairs
+    (x+1, y) with (x, y+1)."""
+    x1, y1 = (x + 1) % Lx, (y + 1) % Ly
+    args = [
+        (env["C1"][x][y], env["T1"][x][y], env["T4"][x][y], A[x][y]),
+        (env["C2"][x1][y], env["T2"][x1][y], env["T1"][x1][y], rot_A(A[x1][y])),
+        (env["C3"][x1][y1], env["T3"][x1][y1], env["T2"][x1][y1], rot_A(rot_A(A[x1][y1]))),
+        (env["C4"][x][y1], env["T4"][x][y1], env["T3"][x][y1], rot_A(rot_A(rot_A(A[x][y1])))),
+    ]
+    opened = (0, 2) if which == 1 else (1, 3)
+    Q = [corner_open(*a) if i in opened else corner_ul(*a) for i, a in enumerate(args)]
+    if which == 1:
+        R = torch.einsum("abst,bc->acst", Q[0], Q[1])
+        Y = torch.einsum("ceuv,ea->cauv", Q[2], Q[3])
+    else:
+        R = torch.einsum("ab,bcst->acst", Q[0], Q[1])
+        Y = torch.einsum("ce,eauv->cauv", Q[2], Q[3])
+    return torch.einsum("acst,cauv->stuv", R, Y)
+
+
 def bond_value(rho, h):
     """Tr(rho h) / Tr(rho) with rho[k1, b1, k2, b2] and h[(b1 b2), (k1 k2)]."""
     d = rho.shape[0]
@@ -83,15 +124,20 @@ def site_value(rho, h):
 
 
 def energy_terms(Lx, Ly, A, env, ham):
-    """Per-site (x, y) -> (e_h, e_v, e_site) before the per-site scale."""
+    """Per-site (x, y) -> [e_h, e_v, e_site, e_diagonals] before the per-site scale."""
     h = torch.as_tensor(np.asarray(ham["h"]), dtype=DT)
     v = torch.as_tensor(np.asarray(ham["v"]), dtype=DT)
     hs = None if ham.get("site") is None else torch.as_tensor(np.asarray(ham["site"]), dtype=DT)
+    nnn = [None if ham.get(k) is None else torch.as_tensor(np.asarray(ham[k]), dtype=DT) for k in ("d1", "d2")]
     out = {}
     for x in range(Lx):
         for y in range(Ly):
             out[x, y] = [bond_value(rho_h(Lx, Ly, A, env, x, y), h), None,
-                         site_value(rho_1(A, env, x, y), hs) if hs is not None else torch.zeros((), dtype=DT)]
+                         site_value(rho_1(A, env, x, y), hs) if hs is not None else torch.zeros((), dtype=DT),
+                         torch.zeros((), dtype=DT)]
+            for which, op in ((1, nnn[0]), (2, nnn[1])):
+                if op is not None:
+                    out[x, y][3] = out[x, y][3] + bond_value(rho_diag(Lx, Ly, A, env, x, y, which), op)
     # vertical bonds: rotate counter-clockwise; site (x, y) -> (y, -x mod Lx) and
     # its lower neighbour becomes its right neighbour
     Lx2, Ly2, A2, env2 = rotate(Lx, Ly, A, env)
@@ -104,5 +150,5 @@ def energy_terms(Lx, Ly, A, env, ham):
 
 def energy(Lx, Ly, A, env, ham):
     terms = energy_terms(Lx, Ly, A, env, ham)
-    tot = sum(t[0] + t[1] + t[2] for t in terms.values())
+    tot = sum(t[0] + t[1] + t[2] + t[3] for t in terms.values())
     return ham.get("scale", 1.0) * tot / (Lx * Ly)

@@ -94,6 +94,32 @@ def cylinder_rdms(A, W):
     return rho_h, rho_v, lam
 
 
+def cylinder_diag_rdms(A, W):
+    """Exact density matrices rho[k1, b1, k2, b2] (trace one) of the diagonal
+    pair (x, y)-(x+1, y+1) and of the anti-diagonal pair (x+1, y)-(x, y+1) on the
+    infinite cylinder of circumference W (W >= 2)."""
+    d = A.shape[0]
+    a = _site(A)
+    T = _column([a] * W)
+    ev, vr = np.linalg.eig(T)
+    vR = vr[:, np.argmax(np.abs(ev))].real
+    evl, vl = np.linalg.eig(T.T)
+    vL = vl[:, np.argmax(np.abs(evl))].real
+    norm2 = vL @ T @ T @ vR
+    row0 = {(k, b): _column([_site(A, (k, b))] + [a] * (W - 1)) for k in range(d) for b in range(d)}
+    row1 = {(k, b): _column([a, _site(A, (k, b))] + [a] * (W - 2)) for k in range(d) for b in range(d)}
+    rho1 = np.zeros((d, d, d, d))
+    rho2 = np.zeros((d, d, d, d))
+    for k1 in range(d):
+        for b1 in range(d):
+            for k2 in range(d):
+                for b2 in range(d):
+                    # column x then column x+1; rows grow downwards
+                    rho1[k1, b1, k2, b2] = vL @ row0[k1, b1] @ row1[k2, b2] @ vR / norm2
+                    rho2[k1, b1, k2, b2] = vL @ row1[k2, b2] @ row0[k1, b1] @ vR / norm2
+    return rho1, rho2
+
+
 def bond_energy(rho, h):
     d = rho.shape[0]
     hh = h.reshape(d, d, d, d)                       # [b1, b2, k1, k2]

@@ -14,6 +14,8 @@ A Hamiltonian is a dict:
   'h'    : (d*d, d*d) horizontal bond operator on (left site, right site),
   'v'    : (d*d, d*d) vertical bond operator on (upper site, lower site),
   'site' : (d, d) on-site operator or None,
+  'd1', 'd2' (optional): (d*d, d*d) operators on the diagonal (x, y)-(x+1, y+1)
+           and the anti-diagonal (x+1, y)-(x, y+1) pairs of every plaquette,
   'scale': factor turning the per-tensor sum into the per-site energy.
 Matrix convention: op[(b1*d + b2), (k1*d + k2)] = <b1 b2| op |k1 k2>.
 
@@ -39,6 +41,16 @@ def heisenberg_bond(rotated: bool) -> np.ndarray:
 def heisenberg(rotated: bool = True, J: float = 1.0) -> dict:
     h = J * heisenberg_bond(rotated)
     return {"h": h, "v": h.copy(), "site": None, "scale": 1.0}
+
+
+def j1j2(J1: float, J2: float, rotated: bool = True) -> dict:
+    """J1-J2 Heisenberg model: J1 S.S on nearest-neighbour bonds (rotated frame
+    as heisenberg()), J2 S.S on both diagonals.  Diagonal neighbours sit on the
+    same sublattice, so the sublattice rotation leaves their bond unrotated."""
+    ham = heisenberg(rotated, J1)
+    ham["d1"] = J2 * heisenberg_bond(False)
+    ham["d2"] = ham["d1"].copy()
+    return ham
 
 
 def kitaev_dimer(K: float = -1.0) -> dict:
