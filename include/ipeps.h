@@ -89,6 +89,18 @@ ipeps_status ipeps_ham_create(int d, const double *h_h, const double *h_v,
 /* Spin-1/2 Heisenberg S.S (J); rotated != 0 applies the sublattice spin flip
  * of Sec. IV.A (second site rotated by i sigma_y), as used with a 1x1 cell. */
 ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out);
+
+/* Next-nearest-neighbour terms (J1-J2 model; S0/S7 of the hot path): h_d1 acts
+ * on the diagonal pair (x, y)-(x+1, y+1), h_d2 on the anti-diagonal pair
+ * (x+1, y)-(x, y+1) of every 2x2 plaquette, each a host (d*d) x (d*d) row-major
+ * matrix in the convention of ipeps_ham_create (copied; NULL removes the
+ * term).  Their expectation values come from the ring of the plaquette's four
+ * enlarged corners with the pair's physical legs open, each normalised by its
+ * own trace, and add to the per-site energy (times the Hamiltonian's scale).
+ * For the Heisenberg J1-J2 model both are J2 S.S, unrotated also in the
+ * sublattice-rotated 1x1 frame (diagonal neighbours share a sublattice).
+ * Errors: IPEPS_ERR_ARG for a NULL Hamiltonian or non-finite entries. */
+ipeps_status ipeps_ham_set_nnn(ipeps_ham ham, const double *h_d1, const double *h_d2);
 /* Spin-1/2 Kitaev model K S^g S^g with two sites (a, b) merged per tensor
  * (d = 4): z link inside the tensor, x link b(x,y)-a(x+1,y), y link
  * b(x,y)-a(x,y+1); energy reported per honeycomb site (scale 1/2). */

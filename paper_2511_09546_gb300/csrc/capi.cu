@@ -164,6 +164,23 @@ ipeps_status ipeps_ham_create(int d, const double *h_h, const double *h_v, const
   });
 }
 
+ipeps_status ipeps_ham_set_nnn(ipeps_ham ham, const double *h_d1, const double *h_d2) {
+  return guarded([&]() {
+    IPEPS_REQUIRE(ham, "ham_set_nnn: NULL Hamiltonian");
+    const int d = ham->impl.d;
+    const size_t n2 = size_t(d) * d * d * d;
+    ham->impl.has_d1 = h_d1 != nullptr;
+    ham->impl.has_d2 = h_d2 != nullptr;
+    if (h_d1) ham->impl.d1.assign(h_d1, h_d1 + n2);
+    else ham->impl.d1.clear();
+    if (h_d2) ham->impl.d2.assign(h_d2, h_d2 + n2);
+    else ham->impl.d2.clear();
+    for (double x : ham->impl.d1) IPEPS_REQUIRE(std::isfinite(x), "ham_set_nnn: non-finite d1");
+    for (double x : ham->impl.d2) IPEPS_REQUIRE(std::isfinite(x), "ham_set_nnn: non-finite d2");
+    return IPEPS_OK;
+  });
+}
+
 ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out) {
   // S.S in the basis |00>,|01>,|10>,|11> (0 = up): 1/4 on the aligned states,
   // -1/4 and the 1/2 exchange on the anti-aligned ones.  The rotated bond

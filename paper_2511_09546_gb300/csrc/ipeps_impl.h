@@ -101,9 +101,11 @@ struct HamImpl {
   double scale = 1.0;
   std::vector<double> h, v, site;  // host copies
   bool has_site = false;
+  std::vector<double> d1, d2;      // diagonal (x,y)-(x+1,y+1), anti-diagonal (x+1,y)-(x,y+1)
+  bool has_d1 = false, has_d2 = false;
 };
 struct HamDev {
-  DBuf h, v, site;
+  DBuf h, v, site, d1, d2;
   HamDev(const HamImpl &H, cudaStream_t s);
 };
 // energy per site on the tape (scalar variable id)

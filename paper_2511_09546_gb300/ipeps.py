@@ -67,6 +67,7 @@ def lib():
         L.ipeps_ham_create.argtypes = [i, dp, dp, dp, d, C.POINTER(vp)]
         L.ipeps_ham_heisenberg.argtypes = [i, d, C.POINTER(vp)]
         L.ipeps_ham_kitaev.argtypes = [d, C.POINTER(vp)]
+        L.ipeps_ham_set_nnn.argtypes = [vp, dp, dp]
         L.ipeps_ham_destroy.argtypes = [vp]
         L.ipeps_ctmrg.argtypes = [sp, vp, i, d, i, i, C.POINTER(vp), C.POINTER(i), dp, vp]
         L.ipeps_env_corner_spectra.argtypes = [vp, dp, C.c_size_t, vp]
@@ -81,7 +82,7 @@ def lib():
         L.ipeps_gemm_noalloc.argtypes = [i, i, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
         L.ipeps_gemm_noalloc.restype = i
         L.ipeps_optimize.argtypes = [sp, vp, vp, C.POINTER(Opts), ITER_CB, vp, vp]
-        for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ctmrg",
+        for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ham_set_nnn", "ipeps_ctmrg",
                      "ipeps_env_corner_spectra", "ipeps_energy", "ipeps_energy_grad",
                      "ipeps_precondition", "ipeps_optimize"):
             getattr(L, name).restype = i
@@ -145,6 +146,24 @@ def ham_heisenberg(rotated=True, J=1.0):
     out = C.c_void_p()
     _check(lib().ipeps_ham_heisenberg(int(rotated), J, C.byref(out)))
     return Ham(out)
+
+
+def ham_set_nnn(ham, d1, d2):
+    """Next-nearest-neighbour operators ((d*d) x (d*d) arrays or None) on the
+    diagonal and anti-diagonal pairs of every plaquette."""
+    dp = C.POINTER(C.c_double)
+    a = None if d1 is None else np.ascontiguousarray(d1, dtype=np.float64)
+    b = None if d2 is None else np.ascontiguousarray(d2, dtype=np.float64)
+    _check(lib().ipeps_ham_set_nnn(ham.h, None if a is None else a.ctypes.data_as(dp),
+                                   None if b is None else b.ctypes.data_as(dp)))
+    return ham
+
+
+def ham_j1j2(J1=1.0, J2=0.5, rotated=True):
+    """J1-J2 Heisenberg model: J1 S.S on nearest neighbours (sublattice-rotated
+    when rotated), J2 S.S on both diagonals (never rotated: same sublattice)."""
+    ss = np.array([[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]])
+    return ham_set_nnn(ham_heisenberg(rotated, J1), J2 * ss, J2 * ss)
 
 
 def ham_kitaev(K=-1.0):
