@@ -126,3 +126,19 @@ def test_convergence_reported():
     cell = inputs.WORKLOADS["heis_d2_chi16"]["gen"]()
     env, it, err = C.ctmrg(cell, 16, tol=1e-10, maxit=300)
     assert err < 1e-10 and it < 300
+
+
+def test_c4v_state_has_equal_bonds():
+    # a tensor symmetric under the 8 operations of the square: horizontal and
+    # vertical bonds carry the same energy
+    rng = np.random.default_rng(6)
+    A = rng.uniform(-1, 1, (2, 2, 2, 2, 2))
+    outs = []
+    for rot in range(4):
+        B = A
+        for _ in range(rot):
+            B = B.transpose(0, 4, 1, 2, 3)
+        outs += [B, B.transpose(0, 1, 4, 3, 2)]
+    A = sum(outs) / 8.0
+    t, _ = _E([[A / np.max(np.abs(A))]], models.heisenberg(False), 12)
+    assert abs(float(t[0, 0][0]) - float(t[0, 0][1])) < 1e-9

@@ -59,3 +59,18 @@ def test_unrolled_converges_to_fixed_point(cfg1):
         errs.append(np.linalg.norm(gu[0][0] - g[0][0]) / np.linalg.norm(g[0][0]))
     assert errs[0] > errs[1] > errs[2]
     assert errs[2] < 1e-6
+
+
+def test_gradient_orthogonal_to_gauge_directions(cfg1):
+    # E is invariant under A -> G on (u, l), G^-1 on (d, r): the gradient is
+    # orthogonal to the infinitesimal directions X A - A X^T on each bond (to the
+    # chi = 16 truncation, which is not gauge covariant: ~5e-6 here, against
+    # ~7e-2 for a random direction)
+    cell, _, _, g, _ = cfg1
+    A, g0 = cell[0][0], g[0][0]
+    rng = np.random.default_rng(4)
+    for _ in range(3):
+        X, Y = rng.standard_normal((2, 2)), rng.standard_normal((2, 2))
+        dA = (np.einsum("uv,svldr->suldr", X, A) - np.einsum("sulvr,vd->suldr", A, X)
+              + np.einsum("lv,suvdr->suldr", Y, A) - np.einsum("suldv,vr->suldr", A, Y))
+        assert abs(np.sum(g0 * dA)) < 1e-4 * np.linalg.norm(g0) * np.linalg.norm(dA)
