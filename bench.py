@@ -309,6 +309,21 @@ def oracle_sample(workload):
     return t_ctm, t_grad, torch.get_num_threads()
 
 
+def cpu_baseline(workload, log, warmup):
+    """The oracle's rate for this run: one oracle CTMRG iteration and one oracle
+    energy + gradient at the workload's size, scaled by the CTMRG iterations
+    and evaluations per L-BFGS step in the GPU run's log (timed steps)."""
+    steps = [r for r in log[warmup + 1:]] or log[1:]
+    ctm_per_step = statistics.mean([max(1, r["ctm_iters"]) * max(1, r["evals"]) for r in steps]) if steps else 29
+    evals_per_step = statistics.mean([max(1, r["evals"]) for r in steps]) if steps else 2
+    t_ctm, t_grad, cores = oracle_sample(workload)
+    v = 1.0 / (t_ctm * ctm_per_step + t_grad * evals_per_step)
+    return {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
+            "sample": f"1 oracle CTMRG iteration ({t_ctm:.2f} s) x {ctm_per_step:.1f} + 1 oracle "
+                      f"energy+gradient ({t_grad:.1f} s) x {evals_per_step:.1f} per L-BFGS step (the GPU "
+                      "run's counts); preconditioner excluded"}
+
+
 def _prec(ipeps, name):
     return {"fp64": ipeps.FP64, "tf32x3": ipeps.TF32X3, "tf32x3_all": ipeps.TF32X3_ALL}[name]
 
@@ -463,18 +478,7 @@ def main():
     rec, log = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            # measured after the GPU run: CTMRG iterations and evaluations per
-            # step from the run's log, one oracle CTMRG iteration and one oracle
-            # energy + gradient at the same size
-            steps = [r for r in log[args.warmup + 1:]] or log[1:]
-            ctm_per_step = statistics.mean([max(1, r["ctm_iters"]) * max(1, r["evals"]) for r in steps]) if steps else 29
-            evals_per_step = statistics.mean([max(1, r["evals"]) for r in steps]) if steps else 2
-            t_ctm, t_grad, cores = oracle_sample(args.workload)
-            v = 1.0 / (t_ctm * ctm_per_step + t_grad * evals_per_step)
-            rec["cpu_baseline"] = {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
-                                   "sample": f"1 oracle CTMRG iteration ({t_ctm:.2f} s) x {ctm_per_step:.1f} + 1 "
-                                             f"oracle energy+gradient ({t_grad:.1f} s) x {evals_per_step:.1f} per "
-                                             "L-BFGS step (the GPU run's counts); preconditioner excluded"}
+            rec["cpu_baseline"] = cpu_baseline(args.workload, log, args.warmup)
         print(json.dumps(rec), flush=True)
     if world > 1:
         torch.distributed.barrier()
