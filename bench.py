@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -53,7 +54,9 @@ class Clocks:
 
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples go to $IPEPS_BENCH_OUT (default: the system temp directory)
+        out_dir = os.environ.get("IPEPS_BENCH_OUT", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -366,7 +369,7 @@ def run_ctmrg(args):
     tf32_peak = peaks.get("bf16_tflops", 1885.7) / 2.0
     n = w["chi"] * w["D"] ** 2
     pairs = 4 * w["Lx"] * w["Ly"]
-    model = pairs * 3 * 2.0 * n ** 3  # the S3 products alone, 2 flop per MAC
+    model = pairs * 3 * 2.0 * n ** 3  # half-system and four-corner products alone, 2 flop per MAC
     flops = sum(v["flops"] for k, v in st.items() if k in ("dgemm", "tc_gemm"))
     gm = st.get("tc_gemm", {"ms": 0.0, "flops": 0.0, "count": 0})
     rec = {"mode": "ctmrg", "workload": args.workload, "precision": args.prec, "iterations": len(lat),

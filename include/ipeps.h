@@ -90,7 +90,7 @@ ipeps_status ipeps_ham_create(int d, const double *h_h, const double *h_v,
  * of Sec. IV.A (second site rotated by i sigma_y), as used with a 1x1 cell. */
 ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out);
 
-/* Next-nearest-neighbour terms (J1-J2 model; S0/S7 of the hot path): h_d1 acts
+/* Next-nearest-neighbour terms (J1-J2 model): h_d1 acts
  * on the diagonal pair (x, y)-(x+1, y+1), h_d2 on the anti-diagonal pair
  * (x+1, y)-(x, y+1) of every 2x2 plaquette, each a host (d*d) x (d*d) row-major
  * matrix in the convention of ipeps_ham_create (copied; NULL removes the

@@ -15,8 +15,7 @@ patch and the right half of site (x+1, y)'s patch; rho_v is rho_h of the
 picture rotated counter-clockwise (the lower site becomes the right site);
 rho_1 is the single-site density matrix of the 3x3 patch.
 
-Next-nearest-neighbour terms (J1-J2 model, the 'h_nnn' of the survey's S0 and
-the 2x2 plaquette of S7): a Hamiltonian with 'd1' / 'd2' operators adds, per
+Next-nearest-neighbour terms (J1-J2 model): a Hamiltonian with 'd1' / 'd2' operators adds, per
 site (x, y), Tr(rho_d1 d1)/Tr rho_d1 for the diagonal (x, y)-(x+1, y+1) and
 Tr(rho_d2 d2)/Tr rho_d2 for the anti-diagonal (x+1, y)-(x, y+1).  Both come
 from the ring of the four enlarged corners of the 2x2 plaquette with upper-left
