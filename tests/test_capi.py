@@ -45,3 +45,21 @@ def test_host_only_calls(lib):
     with pytest.raises(ipeps.IpepsError):
         ipeps.ham_create(2, [[float("nan")] * 4] * 4, [[0.0] * 4] * 4)
     del h, k
+
+
+def test_nnn_setter_host_logic(lib):
+    # the J1-J2 diagonal operators are attached on the host; bad input is reported
+    import ctypes as C
+
+    import numpy as np
+
+    from paper_2511_09546_gb300 import ipeps
+
+    h = ipeps.ham_j1j2(1.0, 0.4, True)
+    ipeps.ham_set_nnn(h, None, np.eye(4))      # one diagonal only
+    ipeps.ham_set_nnn(h, None, None)           # removes both
+    with pytest.raises(ipeps.IpepsError):
+        ipeps.ham_set_nnn(h, np.full((4, 4), np.inf), None)
+    st = ipeps.lib().ipeps_ham_set_nnn(None, None, None)
+    assert st == 1 and b"NULL" in ipeps.lib().ipeps_last_error()
+    del h
