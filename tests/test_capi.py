@@ -49,8 +49,6 @@ def test_host_only_calls(lib):
 
 def test_nnn_setter_host_logic(lib):
     # the J1-J2 diagonal operators are attached on the host; bad input is reported
-    import ctypes as C
-
     import numpy as np
 
     from paper_2511_09546_gb300 import ipeps
