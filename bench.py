@@ -387,6 +387,43 @@ def run_ctmrg(args):
     print(json.dumps(rec), flush=True)
 
 
+def run_ttt(args):
+    """--mode ttt: time to E - E_ref <= 1e-7 from the workload's seeded start,
+    the preconditioned split-precision path against plain FP64 L-BFGS (E_ref
+    from tests/golden/eref_<workload>.json, the oracle's long preconditioned
+    run).  Wall time of the whole optimisation with the device synchronised."""
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import inputs, ipeps
+
+    with open(os.path.join(ROOT, "tests", "golden", f"eref_{args.workload}.json")) as fh:
+        e_ref = json.load(fh)["E_ref"]
+    w = inputs.WORKLOADS[args.workload]
+    A0 = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
+    ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+    out = {"mode": "ttt", "workload": args.workload, "E_ref": e_ref, "tolerance": 1e-7}
+    for name, prec, pre in (("preconditioned_" + args.prec, _prec(ipeps, args.prec), 1),
+                            ("plain_fp64", ipeps.FP64, 0)):
+        opts = ipeps.default_opts(chi=w["chi"], maxiter=args.ttt_maxiter, precondition=pre, ctm_tol=1e-10,
+                                  ctm_maxit=120, prec=prec, gtol=0.0, E_target=e_ref + 1e-7)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, log, status = ipeps.optimize(A0, ham, opts)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        E = log[-1]["E"] if log else float("nan")
+        out[name] = {"seconds": dt, "iterations": len(log) - 1, "evaluations": sum(r["evals"] for r in log),
+                     "E_final": E, "reached": bool(E - e_ref <= 1e-7), "status": status}
+        print(f"[ttt] {name}: {dt:.1f} s, {len(log) - 1} iterations, E - E_ref = {E - e_ref:.3e}",
+              file=sys.stderr, flush=True)
+    a, b = out["preconditioned_" + args.prec], out["plain_fp64"]
+    out["speedup_vs_plain_fp64"] = b["seconds"] / a["seconds"] if a["reached"] and b["reached"] else None
+    print(json.dumps(out), flush=True)
+
+
 def run_gemm(args):
     """--mode gemm: the 3xTF32 tcgen05 GEMM on n x n x n FP64 operands, timed per
     kernel class with CUDA events (W warm-up calls, K timed calls)."""
@@ -435,7 +472,8 @@ def main():
     ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "tf32x3_all"])
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass", "gemm", "ctmrg"])
+    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass", "gemm", "ctmrg", "ttt"])
+    ap.add_argument("--ttt-maxiter", type=int, default=400)
     ap.add_argument("--gemm-n", type=int, default=8192)
     args = ap.parse_args()
     rank, world, local = _dist()
@@ -447,6 +485,9 @@ def main():
         return
     if args.mode == "ctmrg":
         run_ctmrg(args)
+        return
+    if args.mode == "ttt":
+        run_ttt(args)
         return
     if args.impl == "reference":
         if rank != 0:
