@@ -399,7 +399,10 @@ def run_ttt(args):
     entry.build()
     from paper_2511_09546_gb300 import inputs, ipeps
 
-    with open(os.path.join(ROOT, "tests", "golden", f"eref_{args.workload}.json")) as fh:
+    ref = os.path.join(ROOT, "tests", "golden", f"eref_{args.workload}.json")
+    if not os.path.exists(ref):
+        raise SystemExit(f"--mode ttt needs {ref}: write it with tests/golden/make_eref.py")
+    with open(ref) as fh:
         e_ref = json.load(fh)["E_ref"]
     w = inputs.WORKLOADS[args.workload]
     A0 = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
