@@ -243,6 +243,28 @@ def left_move(Lx, Ly, A, env, chi):
     return new
 
 
+def cut_gaps(Lx, Ly, A, env, chi):
+    """(s_chi - s_{chi+1}) / s_1 of the four-corner product M of every projector
+    cut (all four directions, every site).  A gap at rounding level means the
+    kept block of the truncation is not unique (a degenerate cut); parity of
+    gradients is then not asserted."""
+    gaps = []
+    for _ in range(4):
+        for x in range(Lx):
+            for y in range(Ly):
+                x1, y1 = (x + 1) % Lx, (y + 1) % Ly
+                Qul = corner_ul(env["C1"][x][y], env["T1"][x][y], env["T4"][x][y], A[x][y])
+                Qur = corner_ul(env["C2"][x1][y], env["T2"][x1][y], env["T1"][x1][y], rot_A(A[x1][y]))
+                Qlr = corner_ul(env["C3"][x1][y1], env["T3"][x1][y1], env["T2"][x1][y1], rot_A(rot_A(A[x1][y1])))
+                Qll = corner_ul(env["C4"][x][y1], env["T4"][x][y1], env["T3"][x][y1],
+                                rot_A(rot_A(rot_A(A[x][y1]))))
+                S = torch.linalg.svdvals((Qlr @ Qll) @ (Qul @ Qur))
+                if S.numel() > chi:
+                    gaps.append(float((S[chi - 1] - S[chi]) / S[0]))
+        Lx, Ly, A, env = rotate(Lx, Ly, A, env)
+    return gaps
+
+
 def ctmrg_step(Lx, Ly, A, env, chi):
     """One CTMRG iteration: left, top, right and bottom moves."""
     for _ in range(4):

@@ -142,3 +142,14 @@ def test_c4v_state_has_equal_bonds():
     A = sum(outs) / 8.0
     t, _ = _E([[A / np.max(np.abs(A))]], models.heisenberg(False), 12)
     assert abs(float(t[0, 0][0]) - float(t[0, 0][1])) < 1e-9
+
+
+def test_degenerate_cut_detection():
+    # the Neel-like D=4 seed at chi = 64 keeps numerically zero singular values
+    # (degenerate cut); a random D=4 tensor at chi = 32 has a resolvable cut
+    cell = inputs.WORKLOADS["heis_d4_chi64"]["gen"]()
+    env, _, _ = C.ctmrg(cell, 64, tol=1e-10, maxit=200)
+    assert min(C.cut_gaps(1, 1, C.as_torch_cell(cell), env, 64)) < 1e-8
+    cell = inputs.uniform_cell(1, 1, 2, 4, 3)
+    env, _, _ = C.ctmrg(cell, 32, tol=1e-10, maxit=300)
+    assert min(C.cut_gaps(1, 1, C.as_torch_cell(cell), env, 32)) > 1e-8
