@@ -25,6 +25,9 @@
  *     thread-local message from ipeps_last_error().  Inputs are FP64; the
  *     precision enum only selects the arithmetic of the bulk contractions.
  *   - No call launches a kernel that waits on another launch.
+ *   - One device per process: the allocation pool and the 3xTF32 GEMM's
+ *     error word and kernel attributes are set up on the device that is
+ *     current at first use (run one process per GPU, as multi-GPU replicas do).
  */
 #ifndef IPEPS_H
 #define IPEPS_H
