@@ -76,6 +76,25 @@ def rho_1(A, env, x, y):
     return torch.einsum("crwest,crwe->st", L, RC)
 
 
+def norm_per_site(A, env, x=0, y=0):
+    """Norm per site kappa of the iPEPS from the environment of site (x, y):
+    kappa = Z(3x3) Z(2x2) / (Z(3x2) Z(2x3)), the networks of the site's own
+    eight boundary tensors with the double-layer site in the middle, with no
+    site (corners only), and with the middle row or column removed (the facing
+    edge legs joined).  Each boundary tensor appears equally often above and
+    below the fraction line, so their normalisation cancels."""
+    C1, C2, C3, C4 = (env[n][x][y] for n in ("C1", "C2", "C3", "C4"))
+    T1, T2, T3, T4 = (env[n][x][y] for n in ("T1", "T2", "T3", "T4"))
+    a = A[x][y]
+    z9 = torch.einsum("ab,buvc,ce,erwf,fg,gdth,hi,ilma,suldr,svmtw->", C1, T1, C2, T2, C3, T3, C4, T4, a, a)
+    z4 = torch.einsum("ab,bc,cd,da->", C1, C2, C3, C4)
+    # middle row removed: T1's (ket, bra) meet T3's; C2 meets C3, C4 meets C1
+    z6h = torch.einsum("ab,buvc,ce,eg,guvh,ha->", C1, T1, C2, C3, T3, C4)
+    # middle column removed: T2's (ket, bra) meet T4's; C1 meets C2, C3 meets C4
+    z6v = torch.einsum("ab,be,erwf,fg,gh,hrwa->", C1, C2, T2, C3, C4, T4)
+    return z9 * z4 / (z6h * z6v)
+
+
 def corner_open(C1, T1, T4, A):
     """Upper-left enlarged corner with the site's ket and bra physical legs open:
     [(T4.prev, d, d'), (T1.next, r, r'), s, s']."""

@@ -1,6 +1,6 @@
 """Brute-force and closed-form references that pin the oracle (test infrastructure).
 
-* Onsager's nearest-neighbour correlation of the 2D Ising model, reached by
+* Onsager's free energy and nearest-neighbour correlation of the 2D Ising model, reached by
   the 'Ising PEPS' A[s,u,l,d,r] = Q[s,u] Q[s,l] Q[s,d] Q[s,r] with
   Q Q^T = [[e^{K/2}, e^{-K/2}], [e^{-K/2}, e^{K/2}]], whose norm network is
   the Ising partition function at coupling K.
@@ -31,6 +31,26 @@ def onsager_nn(K: float) -> float:
     complete elliptic integral K(k) (scipy takes the parameter m = k^2)."""
     k = 2.0 * np.sinh(2 * K) / np.cosh(2 * K) ** 2
     return 0.5 / np.tanh(2 * K) * (1.0 + (2.0 / np.pi) * (2.0 * np.tanh(2 * K) ** 2 - 1.0) * ellipk(k * k))
+
+
+def onsager_log_z(K: float) -> float:
+    """ln Z / N of the square-lattice Ising model at coupling K (Onsager), as
+    the double integral ln 2 + 1/(8 pi^2) int int ln[cosh^2 2K - sinh 2K (cos a + cos b)]."""
+    from scipy.integrate import dblquad
+    c2, s2 = np.cosh(2 * K) ** 2, np.sinh(2 * K)
+    val, _ = dblquad(lambda a, b: np.log(c2 - s2 * (np.cos(a) + np.cos(b))), 0, 2 * np.pi, 0, 2 * np.pi,
+                     epsabs=1e-13, epsrel=1e-13)
+    return float(np.log(2.0) + val / (8 * np.pi ** 2))
+
+
+def onsager_log_z_1d(K: float) -> float:
+    """The same in Onsager's one-dimensional form:
+    ln(2 cosh 2K) + (1/pi) int_0^{pi/2} ln[(1 + sqrt(1 - k^2 sin^2 t)) / 2] dt, k = 2 sinh 2K / cosh^2 2K."""
+    from scipy.integrate import quad
+    k = 2.0 * np.sinh(2 * K) / np.cosh(2 * K) ** 2
+    val, _ = quad(lambda t: np.log((1.0 + np.sqrt(1.0 - (k * np.sin(t)) ** 2)) / 2.0), 0, np.pi / 2,
+                  epsabs=1e-14, epsrel=1e-14)
+    return float(np.log(2 * np.cosh(2 * K)) + val / np.pi)
 
 
 def _site(A, kb=None):

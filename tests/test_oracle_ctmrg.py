@@ -153,3 +153,15 @@ def test_degenerate_cut_detection():
     cell = inputs.uniform_cell(1, 1, 2, 4, 3)
     env, _, _ = C.ctmrg(cell, 32, tol=1e-10, maxit=300)
     assert min(C.cut_gaps(1, 1, C.as_torch_cell(cell), env, 32)) > 1e-8
+
+
+@pytest.mark.parametrize("K", [0.3, 0.6])
+def test_norm_per_site_is_onsager_free_energy(K):
+    # the Ising PEPS norm network is the Ising partition function, so the CTMRG
+    # norm per site kappa = Z(3x3) Z(2x2) / (Z(3x2) Z(2x3)) gives ln Z / N; the
+    # two published forms of Onsager's result check each other
+    assert abs(exact.onsager_log_z(K) - exact.onsager_log_z_1d(K)) < 1e-12
+    A = exact.ising_peps(K)
+    env, _, _ = C.ctmrg([[A]], 16, tol=1e-11, maxit=600)
+    kappa = float(En.norm_per_site(C.as_torch_cell([[A]]), env))
+    assert abs(np.log(kappa) - exact.onsager_log_z(K)) < 1e-11
