@@ -212,8 +212,9 @@ ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, i
  * loading the library holds until exit.  The caller passes A, B and C only.
  * Requires M * N <= 4194304 (returns IPEPS_ERR_ARG with a message
  * otherwise).  The first call on a device looks up that array's device
- * address with the device current (make that first call before any stream
- * capture); later calls reuse it.  The array keeps the last call's partial
+ * address with that device current and keeps it for the life of the
+ * process (not valid across a cudaDeviceReset); make that first call before
+ * any stream capture.  Later calls reuse the address.  The array keeps the last call's partial
  * sums, each call writes every slice it reads, and calls that overlap on the
  * GPU (other streams or threads) share the array and race: serialise them.
  * Arguments and result as ipeps_gemm with prec = IPEPS_FP64.  Synchronises

@@ -237,7 +237,10 @@ constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 22;  // 4 Mi doubles = 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
 // device address of g_noalloc_scratch for the current device (host code may
-// not use the symbol itself: it is a host-side stand-in, not a device address)
+// not use the symbol itself: it is a host-side stand-in, not a device address).
+// Looked up once per device index and kept for the life of the process: after
+// a cudaDeviceReset (or any reset of the primary context) the cached address
+// is stale, so the entry point must not be used past such a reset.
 double *noalloc_scratch_ptr() {
   static double *ptrs[64] = {nullptr};
   static std::mutex mu;
@@ -274,8 +277,10 @@ void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double 
                 "gemm_noalloc: M*N = " + std::to_string(M * N) + " exceeds the scratch of " +
                     std::to_string(kNoAllocScratchDoubles) + " doubles (32 MiB)");
   const int sms = num_sms();
+  ProfScope prof("dgemm", s, 2.0 * M * N * K, 8.0 * (M * K + K * N + M * N * (beta == 0.0 ? 1.0 : 2.0)));
   if (K == 0) {
     scale_matrix_kernel<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(M, N, beta, C, ldc);
+    count_launch();
     check_launch("gemm_noalloc scale");
     return;
   }
@@ -288,6 +293,7 @@ void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double 
     S = (K + kchunk - 1) / kchunk;
     multidot_kernel<<<unsigned(S), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, W, kchunk);
     splitk_reduce<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
+    count_launch(2);
     check_launch("gemm_noalloc multidot");
     return;
   }
@@ -298,6 +304,7 @@ void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double 
   dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(S));
   dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N, kchunk);
   splitk_reduce<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
+  count_launch(2);
   check_launch("gemm_noalloc splitk");
 }
 }  // namespace ipeps

@@ -24,8 +24,6 @@
 //   * lane 0 of warp 8 streams 32-wide K slices of A' and B' with TMA (128-byte
 //     swizzle) into a ring of shared-memory stages guarded by mbarriers; warp 8
 //     also owns the TMEM allocation (two accumulators, 2 x 128 columns);
-//   * pairs of CTAs along N form a cluster and multicast the A slice they
-//     share, so each CTA reads half of it from L2;
 //   * lane 0 of warp 9 issues tcgen05.mma (M = 128, N = 128, K = 8, four per
 //     slice), releases each stage with tcgen05.commit and signals each
 //     finished chunk on the accumulator's mbarrier.
@@ -160,44 +158,11 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
       : "memory");
 }
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
-// TMA load delivered to the same shared-memory offset (and mbarrier) of every CTA in mask
-__device__ __forceinline__ void tma_load_2d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
-                                               uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "h"(mask)
-      : "memory");
-}
-
-// completion of this CTA's MMAs, arrived on the mbarrier at the same offset in every CTA of mask
-__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(bar)),
-      "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// CL = CTAs per cluster along N.  With CL = 2 the two CTAs of a cluster share
-// the rows m0..m0+127 of A': each loads half of the A slice and multicasts it
-// to both, which halves the A traffic out of L2; a stage is refilled only
-// after the MMAs of both CTAs released it (empty barriers count CL arrivals).
-template <int BN, int CL, bool COMP>
+template <int BN, bool COMP>
 __global__ void __launch_bounds__(threads<BN>(), 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int64_t M, int64_t N, int nk, int chunk, double alpha, double beta,
@@ -205,7 +170,6 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
   constexpr uint32_t A_BYTES = BM * BKT * 4, B_BYTES = BN * BKT * 4;
   constexpr int STAGES = RING_BYTES / int(A_BYTES + B_BYTES);
   constexpr int FLUSH_WARPS = flush_warps<BN>(), PRODUCER_WARP = FLUSH_WARPS, MMA_WARP = FLUSH_WARPS + 1;
-  constexpr uint16_t MASK = uint16_t((1u << CL) - 1);
   static_assert(!COMP || 4 * BN <= TMEM_COLS, "the lo halves need TMEM columns 2 BN .. 3 BN");
   extern __shared__ uint8_t smem_raw[];
   // 1024-byte aligned ring of stages: [A stage | B stage] x STAGES
@@ -213,9 +177,9 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
   __shared__ uint64_t full[STAGES], empty[STAGES], acc_full[2], acc_empty[2];
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int mt = blockIdx.y, ntile = blockIdx.x;
-  if (CL == 1) {
-    // grouped raster: consecutive CTAs walk GROUP_M tile rows column by column
+  // grouped raster: consecutive CTAs walk GROUP_M tile rows column by column
+  int mt, ntile;
+  {
     const int nt = gridDim.x, mtiles = gridDim.y;
     const int id = blockIdx.y * nt + blockIdx.x, per = GROUP_M * nt;
     const int first = (id / per) * GROUP_M, rows = min(GROUP_M, mtiles - first);
@@ -224,12 +188,11 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
   }
   const int m0 = mt * BM, n0 = ntile * BN;
   const int nchunks = (nk + chunk - 1) / chunk;
-  const uint32_t crank = CL > 1 ? cluster_rank() : 0u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CL);
+      mbar_init(&empty[s], 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
@@ -246,7 +209,6 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (CL > 1) cluster_sync();  // peers' barriers are initialised before any multicast reaches them
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = tmem_base;
 
@@ -258,13 +220,7 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
         if (!mbar_wait(&empty[s], ((kt / STAGES) & 1) ^ 1, err)) break;
         uint8_t *sa = base + size_t(s) * (A_BYTES + B_BYTES);
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-        if (CL == 1) {
-          tma_load_2d(sa, &mapA, &full[s], kt * BKT, m0);
-        } else {
-          // rows m0 + crank*BM/CL .. +BM/CL of the slice, to this offset in every CTA of the cluster
-          tma_load_2d_mc(sa + crank * (A_BYTES / CL), &mapA, &full[s], kt * BKT, m0 + int(crank) * (BM / CL),
-                         MASK);
-        }
+        tma_load_2d(sa, &mapA, &full[s], kt * BKT, m0);
         tma_load_2d(sa + A_BYTES, &mapB, &full[s], kt * BKT, n0);
         issued = kt + 1;
       }
@@ -292,8 +248,7 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
 #pragma unroll
           for (int ks = 0; ks < BKT / 8; ++ks)  // 8 TF32 = 32 bytes per MMA: +2 in the address field
             mma_tf32(acc, ad + 2 * ks, bd + 2 * ks, idesc, (kt != k_first || ks != 0) ? 1u : 0u);
-          if (CL == 1) mma_commit(&empty[s]);
-          else mma_commit_mc(&empty[s], MASK);
+          mma_commit(&empty[s]);
         }
         if (ok) mma_commit(&acc_full[b]);
       }
@@ -376,7 +331,6 @@ __global__ void __launch_bounds__(threads<BN>(), 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (CL > 1) cluster_sync();  // no CTA leaves while a peer may still write its shared memory
   if (warp == PRODUCER_WARP) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(uint32_t(TMEM_COLS))
@@ -459,14 +413,14 @@ int *error_word(cudaStream_t s) {
   return w;
 }
 
-template <int BN, int CL, bool COMP>
+template <int BN, bool COMP>
 void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, int64_t Np, int nk, int chunk,
             double alpha, double beta, double *C, int64_t ldc, int *err, cudaStream_t s) {
   constexpr size_t stage = size_t(BM + BN) * BKT * 4;
   constexpr size_t smem = (RING_BYTES / stage) * stage + 1024;
   static bool attr = false;
   if (!attr) {
-    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, CL, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
     attr = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -474,14 +428,9 @@ void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, 
   cfg.blockDim = dim3(threads<BN>());
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = CL;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  IPEPS_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, CL, COMP>, ma, mb, M, N, nk, chunk, alpha, beta,
+  cfg.attrs = nullptr;
+  cfg.numAttrs = 0;
+  IPEPS_CUDA(cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, COMP>, ma, mb, M, N, nk, chunk, alpha, beta,
                                 C, ldc, err));
   count_launch();
   check_launch("tc_gemm");
@@ -492,15 +441,6 @@ bool compensated() {
   static bool c = [] {
     const char *e = std::getenv("IPEPS_TC_COMP");
     return !(e && std::atoi(e) == 0);
-  }();
-  return c;
-}
-
-int cluster_n() {
-  // CTAs per cluster along N (1 or 2): TMA multicast of the shared A slice
-  static int c = [] {
-    const char *e = std::getenv("IPEPS_TC_CLUSTER");
-    return (e && std::atoi(e) == 2) ? 2 : 1;
   }();
   return c;
 }
@@ -526,11 +466,10 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
   }
   IPEPS_REQUIRE((M + BM - 1) / BM <= 65535, "tc_gemm: M too large");
   const int64_t Kp = (K + BKT - 1) / BKT * BKT, Kt = 3 * Kp;
-  const int cl = cluster_n();
   // wide outputs: 192-column tiles (less shared-memory traffic per MMA),
   // plain FP32 sum over chunks; narrow outputs: 128-column tiles, compensated
   const int bn = N > 128 ? 192 : 128;
-  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + cl * bn - 1) / (cl * bn) * (cl * bn);
+  const int64_t Mp = (M + BM - 1) / BM * BM, Np = (N + bn - 1) / bn * bn;
   IPEPS_REQUIRE(Kt / BKT <= 2147483647 && Kp / 32 <= 2147483647, "tc_gemm: K too large");
   float *Ap = static_cast<float *>(dev_alloc(size_t(Mp) * Kt * sizeof(float), s));
   float *Bp = static_cast<float *>(dev_alloc(size_t(Np) * Kt * sizeof(float), s));
@@ -544,19 +483,16 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
     count_launch(2);
     check_launch("tc_pack");
   }
-  const CUtensorMap ma = make_map(Ap, Mp, Kt, BM / cl);
+  const CUtensorMap ma = make_map(Ap, Mp, Kt, BM);
   const CUtensorMap mb = make_map(Bp, Np, Kt, bn);
   int *err = error_word(s);
   {
     ProfScope prof("tc_gemm", s, 2.0 * M * N * K, 4.0 * (Mp + Np) * Kt + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
     const int nk = int(Kt / BKT), ch = chunk_slices();
     const bool comp = compensated();
-    if (bn == 192 && cl == 2) launch<192, 2, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else if (bn == 192) launch<192, 1, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else if (cl == 2 && comp) launch<128, 2, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else if (cl == 2) launch<128, 2, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else if (comp) launch<128, 1, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
-    else launch<128, 1, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    if (bn == 192) launch<192, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else if (comp) launch<128, true>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
+    else launch<128, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);
   }
   int h = 0;
   IPEPS_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -295,7 +295,8 @@ def gemm(A, B, ta=False, tb=False, alpha=1.0, beta=0.0, C=None, prec=FP64):
     if K != K2:
         raise ValueError("inner dimensions differ")
     if C is None:
-        C = torch.zeros((M, N), dtype=torch.float64, device="cuda")
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    _check_out(C, M, N, A.device)
     _check(lib().ipeps_gemm(prec, int(ta), int(tb), M, N, K, alpha, C_ptr(A), A.shape[1], C_ptr(B), B.shape[1],
                             beta, C_ptr(C), C.shape[1], _stream()))
     return C
@@ -305,11 +306,31 @@ def C_ptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def _check_out(C, M, N, device):
+    """C must be a contiguous float64 CUDA tensor of shape (M, N) on `device`:
+    the library writes M x N doubles at its address with row stride N."""
+    if not (isinstance(C, torch.Tensor) and C.is_cuda and C.dtype == torch.float64 and C.is_contiguous()):
+        raise TypeError("C must be a contiguous float64 CUDA tensor")
+    if tuple(C.shape) != (M, N):
+        raise ValueError(f"C has shape {tuple(C.shape)}, expected {(M, N)}")
+    if C.device != device:
+        raise ValueError("C is on another device than A")
+
+
 def gemm_noalloc(A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0):
     """C = alpha op(A) op(B) + beta C through the allocation-free FP64 entry point
     (C is written in place; the library allocates no device memory for it)."""
+    A = _dev(A)
+    B = _dev(B)
+    if A.dim() != 2 or B.dim() != 2:
+        raise ValueError("A and B must be matrices")
     M, K = (A.shape[1], A.shape[0]) if ta else (A.shape[0], A.shape[1])
-    N = B.shape[0] if tb else B.shape[1]
+    K2, N = (B.shape[1], B.shape[0]) if tb else (B.shape[0], B.shape[1])
+    if K != K2:
+        raise ValueError("inner dimensions differ")
+    if B.device != A.device:
+        raise ValueError("A and B are on different devices")
+    _check_out(C, M, N, A.device)
     _check(lib().ipeps_gemm_noalloc(int(ta), int(tb), M, N, K, alpha, C_ptr(A), A.shape[1], C_ptr(B),
                                     B.shape[1], beta, C_ptr(C), C.shape[1], _stream()))
     return C
