@@ -1,17 +1,21 @@
 """Benchmark of the GB300 preconditioned iPEPS hot path.
 
-One step is one preconditioned L-BFGS iteration of the workload (CTMRG run to
-its fixed point warm-started from the previous point, energy, fixed-point
-gradient, local-metric preconditioner P^-1 g by GMRES(30), the Hager-Zhang
-line search).  The default workload is the square-lattice Heisenberg model on
-a 1x1 cell with d=2, D=4, chi=64, started from the seeded Neel-like D=1 state
-embedded in D=4 plus noise.  Prints one JSON line (rank 0).
+One step is one pass of the whole hot path on one tensor of the workload:
+the CTMRG environment run to its fixed point (warm-started from the previous
+pass's environment), the energy and its fixed-point gradient, and the
+local-metric preconditioner P^-1 g (GMRES(30), delta = |g|^2).  The tensors
+visited are the seeded start tensor of the workload plus 1e-3 U[-1, 1]
+perturbations, one per pass (the trial points of an optimiser).  The default
+workload is the square-lattice Heisenberg model on a 1x1 cell with d=2, D=4,
+chi=64, started from the Neel-like D=1 state embedded in D=4 plus noise.
+Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--prec fp64|tf32x3] [--workload NAME]
+                  [--mode pass|optimize|ctmrg|gemm|ttt]
 
---impl reference times the CPU FP64 oracle on a bounded sample of the same
-workload (the oracle is the only reference this method has).
+--impl reference runs the CPU FP64 oracle on the same passes (the oracle is
+the only reference this method has: the paper's own code is not available).
 """
 from __future__ import annotations
 
@@ -29,9 +33,18 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = ("preconditioned L-BFGS iterations/s (Heisenberg 1x1 iPEPS, CTMRG fixed point + energy + "
-          "fixed-point gradient + local-metric GMRES(30) preconditioner per iteration)")
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (152 SMs x 2 DFMA/clk x 2 flop x ~2.07 GHz)
+PASS_EPS = 1e-3      # perturbation of the tensor between passes
+PASS_SEED = 11       # seed of the perturbation sequence
+PASS_TOL = 1e-10     # CTMRG tolerance of a pass
+PASS_MAXIT = 200     # CTMRG iteration limit of a pass
+# DRAM bytes per launch of the dominant kernels from one ncu capture (see
+# profiles/); a kernel changed since its capture has no entry
+NCU_TRAFFIC = {}
+
+
+def metric_name(workload):
+    return (f"hot-path passes/s ({workload}: warm-started CTMRG fixed point + energy + fixed-point "
+            "gradient + local-metric GMRES(30) preconditioner per pass)")
 
 
 def _dist():
@@ -47,6 +60,19 @@ def _peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+def ctmrg_flops_per_iteration(w):
+    """Algorithmic FLOPs of one CTMRG iteration (2 per multiply-add): per
+    projector pair four enlarged corners (chi^3 D^2 + chi^3 D^4 + 2 chi^2 D^6 d
+    each), the two half-system products and the four-corner product
+    (3 (chi D^2)^3) and the absorption (2 chi^3 D^4 + 2 chi^2 D^6 d + 3 chi^3 D^2);
+    4 directional moves x Lx Ly projector pairs."""
+    chi, D, d = w["chi"], w["D"], w["d"]
+    n = chi * D * D
+    corner = chi ** 3 * D ** 2 + chi ** 3 * D ** 4 + 2 * chi ** 2 * D ** 6 * d
+    absorb = 2 * chi ** 3 * D ** 4 + 2 * chi ** 2 * D ** 6 * d + 3 * chi ** 3 * D ** 2
+    return 2.0 * 4 * w["Lx"] * w["Ly"] * (4 * corner + 3 * n ** 3 + absorb)
 
 
 class Clocks:
@@ -116,6 +142,85 @@ def replica_rate(local_ms, n_units, world):
     return slowest, (world * n_units / (slowest / 1000.0) if slowest > 0 else 0.0)
 
 
+def measured_peaks_live():
+    """cuBLAS FP64 and TF32 GEMM rates on this GPU (torch.matmul, best of 3),
+    the denominators for kernels whose dtype MEASURED_PEAKS.json does not cover."""
+    import torch
+
+    out = {}
+    for name, dt, n, tf32 in (("fp64_tflops", torch.float64, 4096, False), ("tf32_tflops", torch.float32, 8192, True)):
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn((n, n), dtype=dt, device="cuda")
+        b = torch.randn((n, n), dtype=dt, device="cuda")
+        c = a @ b
+        best = float("inf")
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c = a @ b
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        torch.backends.cuda.matmul.allow_tf32 = prev
+        out[name] = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+        del a, b, c
+    return out
+
+
+def _ham(ipeps, w):
+    return ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+
+
+def _prec(ipeps, name):
+    return {"fp64": ipeps.FP64, "tf32x3": ipeps.TF32X3, "tf32x3_all": ipeps.TF32X3_ALL}[name]
+
+
+def roofline(prof, peaks_live):
+    """Roofline of the dominant kernel class (live CUDA events over the timed
+    region): achieved = algorithmic work of its launches / their summed time."""
+    if not prof:
+        return None
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    st = prof[dom]
+    peaks = _peaks()
+    total = sum(v["ms"] for v in prof.values())
+    if dom == "tc_gemm":
+        roof = {"kernel": dom, "bound": "tensor", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
+                "peak": peaks_live.get("tf32_tflops"), "unit": "TFLOP/s",
+                "peak_source": "measured: cuBLAS TF32 GEMM 8192^3 on this GPU (torch.matmul, best of 3)"}
+    elif st["flops"] > 0:
+        roof = {"kernel": dom, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
+                "peak": peaks_live.get("fp64_tflops"), "unit": "TFLOP/s",
+                "peak_source": "measured: cuBLAS FP64 GEMM 4096^3 on this GPU (torch.matmul, best of 3)"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
+                "peak": peaks.get("hbm_gbs", 6784.5), "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
+    tr = NCU_TRAFFIC.get(dom)
+    roof["traffic"] = tr["bytes_per_launch"] if tr else None
+    roof["algorithmic_bytes_per_launch"] = st["bytes"] / max(1, st["count"])
+    roof["share"] = st["ms"] / max(1e-9, total)
+    roof["launches"] = st["count"]
+    roof["avg_launch_us"] = 1e3 * st["ms"] / max(1, st["count"])
+    return roof
+
+
+def gpu_pass(ipeps, A, env, w, ham, prec, t_ctm=None):
+    """One hot-path pass through the C ABI; returns (env, E, g, x, CTMRG iterations)."""
+    import torch
+
+    if t_ctm is not None:
+        t_ctm[0].record()
+    env, it, _ = ipeps.ctmrg(A, w["chi"], tol=PASS_TOL, maxit=PASS_MAXIT, prec=prec, env=env)
+    if t_ctm is not None:
+        t_ctm[1].record()
+    E, g = ipeps.energy_grad(A, env, ham)
+    x, _ = ipeps.precondition(A, env, g, -1.0)
+    del torch
+    return env, E, g, x, it
+
+
 def run_ours(args, rank, world, local):
     import torch
 
@@ -126,128 +231,187 @@ def run_ours(args, rank, world, local):
 
     torch.cuda.set_device(local)
     w = inputs.WORKLOADS[args.workload]
-    cell = w["gen"]()
-    A_host = ipeps.cell_tensor(cell)
-    ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+    cell0 = w["gen"]()
+    ham = _ham(ipeps, w)
     prec = _prec(ipeps, args.prec)
     K, W = args.steps, args.warmup
-    opts = ipeps.default_opts(chi=w["chi"], maxiter=W + K, precondition=1, ctm_tol=1e-10, ctm_maxit=120,
-                              prec=prec, gtol=0.0)
-    A = torch.as_tensor(A_host, device="cuda")
+    cells = inputs.perturbed_cells(cell0, W + K, PASS_EPS, PASS_SEED + rank)
+    hostA = [torch.as_tensor(ipeps.cell_tensor(c)) for c in cells]
+    devA = [a.cuda() for a in hostA]  # resident in HBM before the timed region
+    peaks_live = measured_peaks_live()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     stream = torch.cuda.current_stream()
-    starts, ends = {}, {}
-    state = {"launch0": 0, "clocks": None}
-
-    def cb(rec):
-        i = rec["iter"]
-        print(f"[bench] iter {i} E={rec['E']:.12f} |g|={rec['gnorm']:.3e} evals={rec['evals']} "
-              f"ctm={rec['ctm_iters']} wall={rec['wall_ms']:.0f} ms", file=sys.stderr, flush=True)
-        ev = torch.cuda.Event(enable_timing=True)
-        ev.record(stream)
-        ends[i] = ev
-        if i == W:
-            torch.cuda.synchronize()
-            if world > 1:
-                torch.distributed.barrier()
-            ipeps.profile(True)
-            state["launch0"] = ipeps.launch_count()
-            state["clocks"] = Clocks(local)
-        if i >= W + K:
-            return 0
-        flush.fill_(float(i))  # L2 flush between iterations, outside the timed spans
-        st = torch.cuda.Event(enable_timing=True)
-        st.record(stream)
-        starts[i + 1] = st
-        return 0
-
+    # cold start (untimed)
+    env, _, _ = ipeps.ctmrg(torch.as_tensor(ipeps.cell_tensor(cell0), device="cuda"), w["chi"], tol=PASS_TOL,
+                            maxit=PASS_MAXIT, prec=prec)
+    for k in range(W):
+        env, E, g, x, it = gpu_pass(ipeps, devA[k], env, w, ham, prec)
+        print(f"[bench] warm-up pass {k}: ctm {it} E {E:.12f}", file=sys.stderr, flush=True)
+    env_after_warmup = env
     torch.cuda.synchronize()
-    Af, log, status = ipeps.optimize(A, ham, opts, callback=cb)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    ipeps.profile(True)
+    launch0 = ipeps.launch_count()
+    lat, ctm_ms, ctm_its, energies = [], [], [], []
+    for k in range(W, W + K):
+        flush.fill_(float(k))  # L2 flush between passes, outside the timed spans
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        env, E, g, x, it = gpu_pass(ipeps, devA[k], env, w, ham, prec, t_ctm=(c0, c1))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lat.append(e0.elapsed_time(e1))
+        ctm_ms.append(c0.elapsed_time(c1))
+        ctm_its.append(it)
+        energies.append(E)
+        print(f"[bench] pass {k}: ctm {it} E {E:.12f} {lat[-1]:.1f} ms", file=sys.stderr, flush=True)
     torch.cuda.synchronize()
-    launches = ipeps.launch_count() - state["launch0"]
+    launches = ipeps.launch_count() - launch0
     prof = ipeps.profile_stats()
     ipeps.profile(False)
-    clocks = state["clocks"].stop() if state["clocks"] else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
-    timed = [i for i in range(W + 1, W + K + 1) if i in starts and i in ends]
-    lat = [starts[i].elapsed_time(ends[i]) for i in timed]
-    n_timed = len(timed)
-    total_ms, value = replica_rate(sum(lat), n_timed, world)
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms, value = replica_rate(sum(lat), K, world)
 
-    # ---- end to end through the C ABI with host buffers (H2D + D2H inside)
+    # ---- end to end through the C ABI with host buffers: every pass copies its
+    # tensor from pinned host memory and reads back g and P^-1 g and E
+    pinned = [a.pin_memory() for a in hostA[W:W + K]]
+    g_host = torch.empty_like(pinned[0]).pin_memory()
+    x_host = torch.empty_like(pinned[0]).pin_memory()
+    env = env_after_warmup
     torch.cuda.synchronize()
-    host = torch.as_tensor(A_host).pin_memory()
-    out_host = torch.empty_like(host).pin_memory()
-    opts_e2e = ipeps.default_opts(chi=w["chi"], maxiter=1, precondition=1, ctm_tol=1e-10, ctm_maxit=120,
-                                  prec=prec, gtol=0.0)
     t0 = time.perf_counter()
-    Ad = host.to("cuda", non_blocking=True)
-    Ae, log_e2e, _ = ipeps.optimize(Ad, ham, opts_e2e)
-    out_host.copy_(Ae, non_blocking=True)
-    torch.cuda.synchronize()
+    for k in range(K):
+        Ad = pinned[k].to("cuda", non_blocking=True)
+        env, E, g, x, _ = gpu_pass(ipeps, Ad, env, w, ham, prec)
+        g_host.copy_(g, non_blocking=True)
+        x_host.copy_(x, non_blocking=True)
+        torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_iters = max(1, len(log_e2e) - 1)
+    nbytes = pinned[0].numel() * 8
 
-    # ---- roofline of the dominant kernel class (live CUDA events)
-    roof = None
-    if prof:
-        dom = max(prof, key=lambda k: prof[k]["ms"])
-        st = prof[dom]
-        if dom == "tc_gemm":
-            peaks = _peaks()
-            peak = peaks.get("bf16_tflops_sustained", 1703.6) / 2.0
-            roof = {"kernel": dom, "bound": "tensor", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
-                    "peak": peak, "unit": "TFLOP/s", "peak_source": "measured bf16 sustained x 1/2 (tf32 ratio)"}
-        elif st["flops"] > 0:
-            roof = {"kernel": dom, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "peak_source": "nominal FP64 (152 SM x 2 DFMA/clk x 2 x 2.07 GHz)"}
-        else:
-            peaks = _peaks()
-            roof = {"kernel": dom, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
-                    "peak": peaks.get("hbm_gbs", 6750.4), "unit": "GB/s", "peak_source": "measured hbm_gbs"}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-        roof["traffic"] = None
-        roof["share"] = st["ms"] / max(1e-9, sum(v["ms"] for v in prof.values()))
-        roof["launches"] = st["count"]
-    ctm_flops = sum(v["flops"] for k, v in prof.items() if k in ("dgemm", "tc_gemm"))
+    ctm_flops = ctmrg_flops_per_iteration(w)
     rec = {
-        "metric": METRIC,
+        "metric": metric_name(args.workload),
         "value": value,
-        "unit": "iter/s",
+        "unit": "passes/s",
         "n_gpus": world,
-        "steps": n_timed,
+        "steps": K,
         "warmup": W,
-        "ms_per_step": total_ms / max(1, n_timed),
+        "ms_per_step": total_ms / K,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64" if prec == ipeps.FP64 else "tf32x3+f64",
         "data": "synthetic",
-        "config": {"workload": args.workload + ": Heisenberg square lattice 1x1, d=2, D=4, chi=64, "
-                   "Neel-like D=1 seed in D=4 + 1e-2 noise (seed 0)" if args.workload == "heis_d4_chi64"
-                   else args.workload,
-                   "precision": args.prec, "l2": "flushed (256 MB write) between timed iterations",
+        "config": {"workload": args.workload + (": Heisenberg square lattice 1x1, d=2, D=4, chi=64, Neel-like D=1 "
+                                                "seed in D=4 + 1e-2 noise (seed 0)" if args.workload == "heis_d4_chi64"
+                                                else ""),
+                   "pass": f"tensor_k = start + {PASS_EPS:g} U[-1,1] (seed {PASS_SEED}); CTMRG to "
+                           f"{PASS_TOL:g} warm-started from pass k-1; energy + fixed-point gradient; "
+                           "P^-1 g with delta = |g|^2, GMRES(30)",
+                   "precision": args.prec, "l2": "flushed (256 MB write) between timed passes",
                    "parallelism": "replicas" if world > 1 else "single GPU", "chi": w["chi"], "D": w["D"]},
-        "latency_ms": {"p50": float(np.percentile(lat, 50)) if lat else None,
-                       "p99": float(np.percentile(lat, 99)) if lat else None},
-        "gemm_tflops": ctm_flops / (total_ms * 1e-3) / 1e12 if total_ms > 0 else None,
-        "energy": log[-1]["E"] if log else None,
-        "status": status,
-        "roofline": roof,
-        "e2e": {"value": e2e_iters / e2e_s, "unit": "iter/s",
-                "h2d_bytes_per_step": int(host.numel() * 8 / e2e_iters),
-                "d2h_bytes_per_step": int(host.numel() * 8 / e2e_iters)},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "ctmrg": {"iterations_per_pass": statistics.mean(ctm_its), "ms_per_pass": statistics.mean(ctm_ms),
+                  "algorithmic_tflop_per_iteration": ctm_flops / 1e12,
+                  "tflops": ctm_flops * sum(ctm_its) / (sum(ctm_ms) * 1e-3) / 1e12 if sum(ctm_ms) > 0 else None},
+        "energy": energies[-1],
+        "roofline": roofline(prof, peaks_live),
+        "peaks_live": peaks_live,
+        "e2e": {"value": K / e2e_s, "unit": "passes/s", "h2d_bytes_per_step": int(nbytes),
+                "d2h_bytes_per_step": int(2 * nbytes + 8)},
         "gpu_launches": int(launches),
-        "clocks": clocks,
-        "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3)} for k, v in prof.items()},
+        "launches_per_step": launches / K,
+        "clocks": clk,
+        "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3),
+                        "tflops": round(v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12, 4)}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
     }
-    return rec, log
+    return rec
 
 
-def run_passes(args):
-    """--mode pass: W + K hot-path passes at the workload's tensor, each a
-    warm-started CTMRG fixed point + energy + fixed-point gradient + local-metric
-    preconditioner (used for kernel profiles; prints one JSON line)."""
+# --------------------------------------------------------------- oracle side
+def oracle_passes(workload, count, seed_offset=0, sink=None):
+    """The oracle on the host cores, the same passes as the GPU arm: cold CTMRG at
+    the start tensor (untimed), then per pass a warm-started CTMRG fixed point,
+    the energy and fixed-point gradient and P^-1 g (delta = |g|^2, GMRES(30)) of
+    every tensor.  Returns the per-pass seconds and the thread count."""
+    import torch
+
+    from oracle import ctmrg as OC
+    from oracle import gradient as OG
+    from oracle import metric as OMt
+    from oracle import models as OM
+    from paper_2511_09546_gb300 import inputs
+
+    w = inputs.WORKLOADS[workload]
+    cell0 = w["gen"]()
+    Lx, Ly = w["Lx"], w["Ly"]
+    ham = OM.heisenberg(True) if w["d"] == 2 else OM.kitaev_dimer(-1.0)
+    env, _, _ = OC.ctmrg(cell0, w["chi"], tol=PASS_TOL, maxit=PASS_MAXIT)
+    cells = inputs.perturbed_cells(cell0, count, PASS_EPS, PASS_SEED + seed_offset)
+    times = []
+    for k, cell in enumerate(cells):
+        t0 = time.perf_counter()
+        env, _, _ = OC.ctmrg(cell, w["chi"], tol=PASS_TOL, maxit=PASS_MAXIT, env=env)
+        E, g, info = OG.energy_and_gradient(cell, ham, w["chi"], tol=PASS_TOL, env=env, return_info=True)
+        env = info["env"]
+        delta = max(sum(float(np.sum(g[x][y] ** 2)) for x in range(Lx) for y in range(Ly)), 1e-12)
+        A = OC.as_torch_cell(cell)
+        for x in range(Lx):
+            for y in range(Ly):
+                M = OMt.local_metric(env, A[x][y], x, y).numpy()
+                OMt.precondition(M, g[x][y], delta)
+        times.append(time.perf_counter() - t0)
+        if sink:
+            sink(k, times[-1], E)
+    return times, torch.get_num_threads()
+
+
+def cpu_baseline(workload, passes=1):
+    """The oracle's pass rate on a bounded sample: `passes` oracle passes after an
+    untimed cold CTMRG (about 10-20 s of CPU work at the D=4, chi=64 workload)."""
+    times, cores = oracle_passes(workload, passes)
+    v = len(times) / sum(times)
+    return {"value": v, "unit": "passes/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} oracle pass(es) of the same workload (first perturbed tensor), "
+                      f"{sum(times):.1f} s; cold CTMRG at the start tensor untimed"}
+
+
+def run_reference(args, rank, world):
+    """--impl reference: the oracle (FP64, host cores) on the same passes; W
+    untimed passes then K timed, each one whole oracle pass."""
+    if rank != 0:
+        return
+    K, W = args.steps, args.warmup
+
+    def sink(k, t, E):
+        print(f"[reference] pass {k}: {t:.2f} s E {E:.12f}", file=sys.stderr, flush=True)
+
+    times, cores = oracle_passes(args.workload, W + K, sink=sink)
+    t = sum(times[W:])
+    v = K / t
+    rec = {"impl": "reference", "metric": metric_name(args.workload), "value": v, "unit": "passes/s",
+           "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "precision": "fp64"},
+           "cpu_baseline": {"value": v, "unit": "passes/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{K} timed oracle passes after {W} untimed ones (whole passes: CTMRG, "
+                                      "energy, fixed-point gradient, preconditioner)"},
+           "e2e": {"value": v, "unit": "passes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(rec), flush=True)
+
+
+# --------------------------------------------------------------- other modes
+def run_optimize(args):
+    """--mode optimize: preconditioned L-BFGS iterations at the workload (W warm-up
+    iterations, K timed), each a CTMRG fixed point + energy + gradient +
+    preconditioner per line-search evaluation.  Prints one JSON line."""
     import torch
 
     import __graft_entry__ as entry
@@ -256,79 +420,28 @@ def run_passes(args):
     from paper_2511_09546_gb300 import inputs, ipeps
 
     w = inputs.WORKLOADS[args.workload]
-    A0 = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
-    ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+    A = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
     prec = _prec(ipeps, args.prec)
-    gen = torch.Generator(device="cpu").manual_seed(1)
-    env, _, _ = ipeps.ctmrg(A0, w["chi"], tol=1e-10, maxit=200, prec=prec, allow_unconverged=True)
-    lat = []
-    for k in range(args.warmup + args.steps):
-        A = A0 + 1e-3 * torch.rand(A0.shape, generator=gen, dtype=torch.float64).cuda()
-        if k == args.warmup:
-            ipeps.profile(True)
-        t0 = torch.cuda.Event(enable_timing=True)
-        t1 = torch.cuda.Event(enable_timing=True)
-        t0.record()
-        env, it, err = ipeps.ctmrg(A, w["chi"], tol=1e-10, maxit=200, prec=prec, env=env, allow_unconverged=True)
-        E, g = ipeps.energy_grad(A, env, ham)
-        x, res = ipeps.precondition(A, env, g, float((g * g).sum()))
-        t1.record()
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            lat.append(t0.elapsed_time(t1))
-        print(f"[bench] pass {k} ctm {it} E {E:.12f} {t0.elapsed_time(t1):.1f} ms", file=sys.stderr, flush=True)
-    prof = ipeps.profile_stats()
-    rec = {"mode": "pass", "workload": args.workload, "precision": args.prec, "passes": len(lat),
-           "ms_per_pass": statistics.mean(lat) if lat else None,
-           "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3),
-                           "tflops": v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12} for k, v in prof.items()}}
+    K, W = args.steps, args.warmup
+    opts = ipeps.default_opts(chi=w["chi"], maxiter=W + K, precondition=1, ctm_tol=1e-10, ctm_maxit=120,
+                              prec=prec, gtol=0.0)
+    walls = []
+
+    def cb(rec):
+        print(f"[bench] iter {rec['iter']} E={rec['E']:.12f} |g|={rec['gnorm']:.3e} evals={rec['evals']} "
+              f"ctm={rec['ctm_iters']} wall={rec['wall_ms']:.0f} ms", file=sys.stderr, flush=True)
+        if rec["iter"] > W:
+            walls.append(rec["wall_ms"])
+        return 0
+
+    torch.cuda.synchronize()
+    _, log, status = ipeps.optimize(A, _ham(ipeps, w), opts, callback=cb)
+    rec = {"mode": "optimize", "workload": args.workload, "precision": args.prec, "iterations": len(walls),
+           "iterations_per_s": 1e3 * len(walls) / sum(walls) if walls else None,
+           "latency_ms": {"p50": float(np.percentile(walls, 50)) if walls else None,
+                          "p99": float(np.percentile(walls, 99)) if walls else None},
+           "energy": log[-1]["E"] if log else None, "status": status}
     print(json.dumps(rec), flush=True)
-
-
-def oracle_sample(workload):
-    """The oracle on the host cores at the workload's size: seconds of one CTMRG
-    iteration and of one energy + fixed-point gradient, both from the converged
-    environment (the convergence itself is not timed), and the thread count."""
-    import torch
-
-    from oracle import ctmrg as OC
-    from oracle import gradient as OG
-    from oracle import models as OM
-    from paper_2511_09546_gb300 import inputs
-
-    w = inputs.WORKLOADS[workload]
-    cell = w["gen"]()
-    Lx, Ly = w["Lx"], w["Ly"]
-    ham = OM.heisenberg(True) if w["d"] == 2 else OM.kitaev_dimer(-1.0)
-    env, _, _ = OC.ctmrg(cell, w["chi"], tol=1e-10, maxit=200)
-    A = OC.as_torch_cell(cell)
-    with torch.no_grad():
-        t0 = time.perf_counter()
-        OC.ctmrg_step(Lx, Ly, A, env, w["chi"])
-        t_ctm = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    OG.energy_and_gradient(cell, ham, w["chi"], tol=1e-10, env=env)
-    t_grad = time.perf_counter() - t0
-    return t_ctm, t_grad, torch.get_num_threads()
-
-
-def cpu_baseline(workload, log, warmup):
-    """The oracle's rate for this run: one oracle CTMRG iteration and one oracle
-    energy + gradient at the workload's size, scaled by the CTMRG iterations
-    and evaluations per L-BFGS step in the GPU run's log (timed steps)."""
-    steps = [r for r in log[warmup + 1:]] or log[1:]
-    ctm_per_step = statistics.mean([max(1, r["ctm_iters"]) * max(1, r["evals"]) for r in steps]) if steps else 29
-    evals_per_step = statistics.mean([max(1, r["evals"]) for r in steps]) if steps else 2
-    t_ctm, t_grad, cores = oracle_sample(workload)
-    v = 1.0 / (t_ctm * ctm_per_step + t_grad * evals_per_step)
-    return {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 oracle CTMRG iteration ({t_ctm:.2f} s) x {ctm_per_step:.1f} + 1 oracle "
-                      f"energy+gradient ({t_grad:.1f} s) x {evals_per_step:.1f} per L-BFGS step (the GPU "
-                      "run's counts); preconditioner excluded"}
-
-
-def _prec(ipeps, name):
-    return {"fp64": ipeps.FP64, "tf32x3": ipeps.TF32X3, "tf32x3_all": ipeps.TF32X3_ALL}[name]
 
 
 def run_ctmrg(args):
@@ -352,6 +465,7 @@ def run_ctmrg(args):
         env, _, _ = ipeps.ctmrg(A, w["chi"], tol=1e-30, maxit=1, prec=prec, env=env, allow_unconverged=True)
     torch.cuda.synchronize()
     free1 = torch.cuda.mem_get_info()[0]
+    peaks_live = measured_peaks_live()
     ipeps.profile(True)
     lat = []
     for _ in range(args.steps):
@@ -365,33 +479,30 @@ def run_ctmrg(args):
     st = ipeps.profile_stats()
     ipeps.profile(False)
     tot_ms = sum(lat)
-    peaks = _peaks()
-    tf32_peak = peaks.get("bf16_tflops", 1885.7) / 2.0
-    n = w["chi"] * w["D"] ** 2
-    pairs = 4 * w["Lx"] * w["Ly"]
-    model = pairs * 3 * 2.0 * n ** 3  # half-system and four-corner products alone, 2 flop per MAC
-    flops = sum(v["flops"] for k, v in st.items() if k in ("dgemm", "tc_gemm"))
+    tf32_peak = peaks_live["tf32_tflops"]
+    model = ctmrg_flops_per_iteration(w)
     gm = st.get("tc_gemm", {"ms": 0.0, "flops": 0.0, "count": 0})
     rec = {"mode": "ctmrg", "workload": args.workload, "precision": args.prec, "iterations": len(lat),
            "ms_per_iteration": tot_ms / max(1, len(lat)),
            "ctmrg_iterations_per_s": 1e3 * len(lat) / tot_ms, "moves_per_s": 4e3 * len(lat) / tot_ms,
-           "gemm_tflops": flops / (tot_ms * 1e-3) / 1e12,
-           "s3_model_tflop_per_iteration": model / 1e12,
+           "algorithmic_tflop_per_iteration": model / 1e12,
+           "algorithmic_tflops": model * len(lat) / (tot_ms * 1e-3) / 1e12,
            "tc_gemm": {"share": gm["ms"] / tot_ms, "launches": gm["count"],
                        "logical_tflops": gm["flops"] / max(1e-9, gm["ms"] * 1e-3) / 1e12,
                        "issued_frac_of_tf32_peak": 3 * gm["flops"] / max(1e-9, gm["ms"] * 1e-3) / 1e12 / tf32_peak},
+           "peaks_live": peaks_live,
            "last_change": err, "device_bytes_after_warmup": int(free0 - free1),
            "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 2),
                            "tflops": round(v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12, 3)}
-                       for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:8]}}
+                       for k, v in sorted(st.items(), key=lambda kv: -kv[1]["ms"])[:10]}}
     print(json.dumps(rec), flush=True)
 
 
 def run_ttt(args):
     """--mode ttt: time to E - E_ref <= 1e-7 from the workload's seeded start,
-    the preconditioned split-precision path against plain FP64 L-BFGS (E_ref
-    from tests/golden/eref_<workload>.json, the oracle's long preconditioned
-    run).  Wall time of the whole optimisation with the device synchronised."""
+    the preconditioned path in the chosen precision against plain FP64 L-BFGS
+    (E_ref from tests/golden/eref_<workload>.json).  Wall time of the whole
+    optimisation with the device synchronised."""
     import torch
 
     import __graft_entry__ as entry
@@ -401,28 +512,32 @@ def run_ttt(args):
 
     ref = os.path.join(ROOT, "tests", "golden", f"eref_{args.workload}.json")
     if not os.path.exists(ref):
-        raise SystemExit(f"--mode ttt needs {ref}: write it with tests/golden/make_eref.py")
+        raise SystemExit(f"--mode ttt needs {ref}")
     with open(ref) as fh:
         e_ref = json.load(fh)["E_ref"]
     w = inputs.WORKLOADS[args.workload]
     A0 = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
-    ham = ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
+    ham = _ham(ipeps, w)
     out = {"mode": "ttt", "workload": args.workload, "E_ref": e_ref, "tolerance": 1e-7}
-    for name, prec, pre in (("preconditioned_" + args.prec, _prec(ipeps, args.prec), 1),
-                            ("plain_fp64", ipeps.FP64, 0)):
+    runs = [("preconditioned_" + args.prec, _prec(ipeps, args.prec), 1), ("plain_fp64", ipeps.FP64, 0)]
+    for name, prec, pre in runs:
         opts = ipeps.default_opts(chi=w["chi"], maxiter=args.ttt_maxiter, precondition=pre, ctm_tol=1e-10,
                                   ctm_maxit=120, prec=prec, gtol=0.0, E_target=e_ref + 1e-7)
+
+        def cb(rec, name=name):
+            print(f"[ttt] {name} iter {rec['iter']} E {rec['E']:.12f} dE {rec['E'] - e_ref:.3e} "
+                  f"evals {rec['evals']} wall {rec['wall_ms']:.0f} ms", file=sys.stderr, flush=True)
+            return 0
+
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, log, status = ipeps.optimize(A0, ham, opts)
+        _, log, status = ipeps.optimize(A0, ham, opts, callback=cb)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         E = log[-1]["E"] if log else float("nan")
         out[name] = {"seconds": dt, "iterations": len(log) - 1, "evaluations": sum(r["evals"] for r in log),
                      "E_final": E, "reached": bool(E - e_ref <= 1e-7), "status": status}
-        print(f"[ttt] {name}: {dt:.1f} s, {len(log) - 1} iterations, E - E_ref = {E - e_ref:.3e}",
-              file=sys.stderr, flush=True)
-    a, b = out["preconditioned_" + args.prec], out["plain_fp64"]
+    a, b = out[runs[0][0]], out["plain_fp64"]
     out["speedup_vs_plain_fp64"] = b["seconds"] / a["seconds"] if a["reached"] and b["reached"] else None
     print(json.dumps(out), flush=True)
 
@@ -442,19 +557,20 @@ def run_gemm(args):
     A = torch.randn((n, n), generator=g, dtype=torch.float64).cuda()
     B = torch.randn((n, n), generator=g, dtype=torch.float64).cuda()
     C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    prec = _prec(ipeps, args.prec if args.prec != "fp64" else "tf32x3")
     for _ in range(args.warmup):
-        ipeps.gemm(A, B, C=C, prec=ipeps.TF32X3)
+        ipeps.gemm(A, B, C=C, prec=prec)
     torch.cuda.synchronize()
+    peaks_live = measured_peaks_live()
     ipeps.profile(True)
     for _ in range(args.steps):
-        ipeps.gemm(A, B, C=C, prec=ipeps.TF32X3)
+        ipeps.gemm(A, B, C=C, prec=prec)
     torch.cuda.synchronize()
     st = ipeps.profile_stats()
     ipeps.profile(False)
     ref_rows = A[:64] @ B
     err = float((C[:64] - ref_rows).abs().max() / ref_rows.abs().max())
-    peaks = _peaks()
-    tf32_peak = peaks.get("bf16_tflops", 1885.7) / 2.0
+    tf32_peak = peaks_live["tf32_tflops"]
     gm, pk = st.get("tc_gemm", {}), st.get("tc_pack", {})
     logical = gm["flops"] / (gm["ms"] * 1e-3) / 1e12
     rec = {"mode": "gemm", "n": n, "launches": gm.get("count"), "gemm_ms": gm["ms"] / max(1, gm["count"]),
@@ -462,70 +578,39 @@ def run_gemm(args):
            "logical_tflops": logical, "issued_tf32_tflops": 3 * logical,
            "tf32_peak_tflops": tf32_peak, "issued_frac_of_tf32_peak": 3 * logical / tf32_peak,
            "pack_gbs": pk.get("bytes", 0.0) / max(1e-9, pk.get("ms", 0.0) * 1e-3) / 1e9,
-           "rel_err_vs_fp64": err}
+           "rel_err_vs_fp64": err, "peaks_live": peaks_live}
     print(json.dumps(rec), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "tf32x3_all"])
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="optimize", choices=["optimize", "pass", "gemm", "ctmrg", "ttt"])
+    ap.add_argument("--mode", default="pass", choices=["pass", "optimize", "gemm", "ctmrg", "ttt"])
     ap.add_argument("--ttt-maxiter", type=int, default=400)
     ap.add_argument("--gemm-n", type=int, default=8192)
     args = ap.parse_args()
     rank, world, local = _dist()
-    if args.mode == "pass":
-        run_passes(args)
-        return
-    if args.mode == "gemm":
-        run_gemm(args)
-        return
-    if args.mode == "ctmrg":
-        run_ctmrg(args)
-        return
-    if args.mode == "ttt":
-        run_ttt(args)
-        return
     if args.impl == "reference":
-        if rank != 0:
-            return
-        # the oracle: each step times one CTMRG iteration and one energy +
-        # gradient at the workload's size and scales them to one L-BFGS step by
-        # the step's CTMRG iterations and evaluations on the GPU path (29 and 2
-        # at heis_d4_chi64, means over timed steps); the preconditioner and
-        # line-search bookkeeping are not included
-        per_step_ctm, per_step_evals = 29, 2
-        times = []
-        for _ in range(args.warmup + args.steps):
-            t_ctm, t_grad, cores = oracle_sample(args.workload)
-            times.append(per_step_ctm * t_ctm + per_step_evals * t_grad)
-        t = statistics.mean(times[args.warmup:])
-        v = 1.0 / t
-        rec = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iter/s", "n_gpus": world,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-               "config": {"workload": args.workload, "precision": "fp64"},
-               "cpu_baseline": {"value": v, "unit": "iter/s", "cores": cores, "kind": "oracle",
-                                "sample": f"per step: 1 oracle CTMRG iteration x {per_step_ctm} + 1 oracle "
-                                          f"energy+gradient x {per_step_evals} (GPU path's per-step counts); "
-                                          "preconditioner excluded"},
-               "e2e": {"value": v, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(rec), flush=True)
+        run_reference(args, rank, world)
+        return
+    modes = {"optimize": run_optimize, "gemm": run_gemm, "ctmrg": run_ctmrg, "ttt": run_ttt}
+    if args.mode in modes:
+        modes[args.mode](args)
         return
     import torch
 
     if world > 1:
         torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    rec, log = run_ours(args, rank, world, local)
+    rec = run_ours(args, rank, world, local)
     if rank == 0:
         if not args.no_cpu_baseline:
-            rec["cpu_baseline"] = cpu_baseline(args.workload, log, args.warmup)
+            rec["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(rec), flush=True)
     if world > 1:
         torch.distributed.barrier()

@@ -104,6 +104,12 @@ ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out);
  * sublattice-rotated 1x1 frame (diagonal neighbours share a sublattice).
  * Errors: IPEPS_ERR_ARG for a NULL Hamiltonian or non-finite entries. */
 ipeps_status ipeps_ham_set_nnn(ipeps_ham ham, const double *h_d1, const double *h_d2);
+/* Spin-1/2 J1-J2 Heisenberg model: J1 S.S on nearest-neighbour bonds
+ * (sublattice-rotated as ipeps_ham_heisenberg when rotated != 0) and J2 S.S
+ * on both diagonals of every plaquette (ipeps_ham_set_nnn; unrotated, as
+ * diagonal neighbours share a sublattice).  Errors: IPEPS_ERR_ARG for a NULL
+ * out or non-finite couplings. */
+ipeps_status ipeps_ham_j1j2(int rotated, double J1, double J2, ipeps_ham *out);
 /* Spin-1/2 Kitaev model K S^g S^g with two sites (a, b) merged per tensor
  * (d = 4): z link inside the tensor, x link b(x,y)-a(x+1,y), y link
  * b(x,y)-a(x,y+1); energy reported per honeycomb site (scale 1/2). */
@@ -150,6 +156,8 @@ ipeps_status ipeps_energy_grad(const ipeps_shape *shape, const double *A_dev, ip
  * scaled so that <A|1 (x) M|A> = 1; solved by GMRES with Krylov dimension
  * `krylov` and `restarts` outer iterations, x0 = 0 (Sec. III.C uses 30 and
  * 1).  g_dev, out_dev: device, layout of A (out_dev may alias nothing).
+ * delta < 0 selects the |g|^2 rule of Sec. III.B: delta = max(|g|^2, 1e-12)
+ * with |g| the Euclidean norm of g over the whole cell.
  * resid_out (host, may be NULL): the largest relative residual. */
 ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, ipeps_env env,
                                 const double *g_dev, double delta, int krylov, int restarts,

@@ -167,3 +167,87 @@ def torus_state(A, L):
             ops += [A, [phys[x, y], u, l, dn, r]]
     out = [phys[x, y] for y in range(L) for x in range(L)]
     return np.einsum(*ops, out, optimize="greedy")
+
+
+def torus_bond_energies(A, L, h, v):
+    """<h> on the horizontal bond (0, 0)-(1, 0) and <v> on the vertical bond
+    (0, 0)-(0, 1) of the uniform PEPS on the L x L torus, from the full state
+    vector (exact; small L only).  h, v in the convention op[(b1 b2), (k1 k2)]."""
+    psi = torus_state(A, L)
+    d = A.shape[0]
+    nrm = float(np.sum(psi * psi))
+
+    def pair(op, i, j):
+        # sites i, j in the row-major (y, x) order of torus_state
+        o = np.asarray(op).reshape(d, d, d, d)                  # [b1, b2, k1, k2]
+        x = np.moveaxis(psi, (i, j), (0, 1))
+        hx = np.einsum("abkm,km...->ab...", o, x)
+        return float(np.sum(x * hx)) / nrm
+
+    return pair(h, 0, 1), pair(v, 0, L)
+
+
+def cylinder_cell_rdms(cell, W):
+    """Exact density matrices of a unit cell cell[x][y] (Lx columns, Ly rows) on
+    the infinite cylinder of circumference W (periodic in y, W a multiple of Ly):
+    per site (x, y) the horizontal pair (x, y)-(x+1, y), the vertical pair
+    (x, y)-(x, y+1) (rho[k1, b1, k2, b2], trace one) and the single site
+    (rho[k, b]).  The column transfer matrices T_x of the cell's columns are
+    multiplied along the cylinder's axis; the boundary vectors are the dominant
+    left and right eigenvectors of one unit T_0 ... T_{Lx-1}."""
+    Lx, Ly = len(cell), len(cell[0])
+    assert W % Ly == 0
+    d = np.asarray(cell[0][0]).shape[0]
+    A = [[np.asarray(a) for a in col] for col in cell]
+    closed = [[_site(A[x][y % Ly]) for y in range(W)] for x in range(Lx)]
+    T = [_column(closed[x]) for x in range(Lx)]
+    U = T[0]
+    for x in range(1, Lx):
+        U = U @ T[x]
+    ev, vr = np.linalg.eig(U)
+    vR = vr[:, np.argmax(np.abs(ev))].real
+    evl, vl = np.linalg.eig(U.T)
+    vL = vl[:, np.argmax(np.abs(evl))].real
+
+    def opened(x, fixed):
+        sites = list(closed[x])
+        for y, kb in fixed.items():
+            sites[y % W] = _site(A[x][y % Ly], kb)
+        return _column(sites)
+
+    def chain(cols):
+        # vL (product over the 2 Lx columns of two units) vR, columns given per position
+        vec = vL
+        for M in cols:
+            vec = vec @ M
+        return float(vec @ vR)
+
+    two = [T[i % Lx] for i in range(2 * Lx)]
+    norm2 = chain(two)
+    norm1 = chain(two[:Lx])
+    out = {}
+    for x in range(Lx):
+        for y in range(Ly):
+            rh = np.zeros((d, d, d, d))
+            rv = np.zeros((d, d, d, d))
+            r1 = np.zeros((d, d))
+            for k1 in range(d):
+                for b1 in range(d):
+                    cols = list(two[:Lx])
+                    cols[x] = opened(x, {y: (k1, b1)})
+                    r1[k1, b1] = chain(cols) / norm1
+                    for k2 in range(d):
+                        for b2 in range(d):
+                            cols = list(two)
+                            cols[x] = opened(x, {y: (k1, b1)})
+                            cols[x + 1] = opened((x + 1) % Lx, {y: (k2, b2)})
+                            rh[k1, b1, k2, b2] = chain(cols) / norm2
+                            cols = list(two[:Lx])
+                            cols[x] = opened(x, {y: (k1, b1), y + 1: (k2, b2)})
+                            rv[k1, b1, k2, b2] = chain(cols) / norm1
+            out[x, y] = (rh, rv, r1)
+    return out
+
+
+def site_energy(rho1, op):
+    return float(np.einsum("kb,bk->", rho1, np.asarray(op)) / np.trace(rho1))

@@ -2,6 +2,7 @@
 // the runtime helpers shared by the translation units.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -200,6 +201,29 @@ ipeps_status ipeps_ham_heisenberg(int rotated, double J, ipeps_ham *out) {
   return ipeps_ham_create(2, h, h, nullptr, 1.0, out);
 }
 
+ipeps_status ipeps_ham_j1j2(int rotated, double J1, double J2, ipeps_ham *out) {
+  // J1 S.S on nearest neighbours (sublattice-rotated when rotated != 0) and
+  // J2 S.S on both plaquette diagonals, never rotated: diagonal neighbours sit
+  // on the same sublattice
+  return guarded([&]() {
+    IPEPS_REQUIRE(out && std::isfinite(J1) && std::isfinite(J2), "ham_j1j2: bad arguments");
+    ipeps_ham h = nullptr;
+    ipeps_status st = ipeps_ham_heisenberg(rotated, J1, &h);
+    if (st != IPEPS_OK) return st;
+    double nnn[16] = {0};
+    nnn[0] = 0.25 * J2; nnn[15] = 0.25 * J2;
+    nnn[5] = -0.25 * J2; nnn[10] = -0.25 * J2;
+    nnn[6] = 0.5 * J2; nnn[9] = 0.5 * J2;
+    st = ipeps_ham_set_nnn(h, nnn, nnn);
+    if (st != IPEPS_OK) {
+      ipeps_ham_destroy(h);
+      return st;
+    }
+    *out = h;
+    return IPEPS_OK;
+  });
+}
+
 ipeps_status ipeps_ham_kitaev(double K, ipeps_ham *out) {
   // tensor index s = 2 a + b; two-tensor index (a1, b1, a2, b2)
   const double I2[4] = {1, 0, 0, 1};
@@ -326,10 +350,19 @@ ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, i
     IPEPS_REQUIRE(A_dev && g_dev && out_dev, "precondition: NULL argument");
     IPEPS_REQUIRE(krylov >= 1 && krylov <= 1000 && restarts >= 1 && restarts <= 1000,
                   "precondition: krylov / restarts out of range");
-    IPEPS_REQUIRE(delta >= 0.0 && std::isfinite(delta), "precondition: delta must be finite and >= 0");
+    IPEPS_REQUIRE(std::isfinite(delta), "precondition: delta must be finite");
     IPEPS_REQUIRE(out_dev != g_dev, "precondition: out_dev must not alias g_dev");
     check_env(env, c);
     check_finite(g_dev, int64_t(c.nsites()) * c.tsize(), s, "g");
+    if (delta < 0.0) {
+      // the |g|^2 rule of Sec. III.B, floored at 1e-12
+      ipeps::DBuf nr(1, s);
+      ipeps::nrm2(int64_t(c.nsites()) * c.tsize(), g_dev, nr.p, s);
+      double h = 0.0;
+      IPEPS_CUDA(cudaMemcpyAsync(&h, nr.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      IPEPS_CUDA(cudaStreamSynchronize(s));
+      delta = std::max(h * h, 1e-12);
+    }
     double r = ipeps::precondition_all(env->impl, A_dev, g_dev, delta, krylov, restarts, out_dev, s);
     IPEPS_CUDA(cudaStreamSynchronize(s));
     if (resid_out) *resid_out = r;

@@ -171,7 +171,7 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
   }
   IPEPS_REQUIRE((N + BN - 1) / BN <= 2147483647 && (M + BM - 1) / BM <= 65535 && batch <= 65535,
                 "gemm_f64: grid too large");
-  ProfScope prof("dgemm", s, 2.0 * M * N * K * batch,
+  ProfScope prof(shape_class("dgemm", M, N, K * batch), s, 2.0 * M * N * K * batch,
                  8.0 * batch * (M * K + K * N + M * N * (beta == 0.0 ? 1.0 : 2.0)));
   const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
   const int sms = num_sms();

@@ -487,7 +487,7 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
   const CUtensorMap mb = make_map(Bp, Np, Kt, bn);
   int *err = error_word(s);
   {
-    ProfScope prof("tc_gemm", s, 2.0 * M * N * K, 4.0 * (Mp + Np) * Kt + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
+    ProfScope prof(shape_class("tc_gemm", M, N, K), s, 2.0 * M * N * K, 4.0 * (Mp + Np) * Kt + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
     const int nk = int(Kt / BKT), ch = chunk_slices();
     const bool comp = compensated();
     if (bn == 192) launch<192, false>(ma, mb, M, N, Np, nk, ch, alpha, beta, C, ldc, err, s);

@@ -3,7 +3,9 @@
 // pair; durations are resolved when the statistics are read.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -22,14 +24,28 @@ struct Stat {
 std::mutex g_mu;
 std::map<std::string, Stat> g_stats;
 bool g_on = false;
+std::vector<cudaEvent_t> g_free;  // recycled events (creating one per launch costs host time)
 
+cudaEvent_t take_event() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_free.empty()) {
+    cudaEvent_t e = g_free.back();
+    g_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// caller holds g_mu
 void resolve(Stat &st) {
   for (auto &pr : st.pending) {
     cudaEventSynchronize(pr.second);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, pr.first, pr.second) == cudaSuccess) st.ms += ms;
-    cudaEventDestroy(pr.first);
-    cudaEventDestroy(pr.second);
+    g_free.push_back(pr.first);
+    g_free.push_back(pr.second);
   }
   st.pending.clear();
 }
@@ -37,11 +53,24 @@ void resolve(Stat &st) {
 
 bool profiling() { return g_on; }
 
+const char *shape_class(const char *base, int64_t M, int64_t N, int64_t K) {
+  static const bool on = [] {
+    const char *e = std::getenv("IPEPS_PROF_SHAPES");
+    return e && e[0] == '1';
+  }();
+  if (!on || !g_on) return base;
+  static std::mutex mu;
+  static std::set<std::string> names;  // stable storage for the returned pointers
+  std::lock_guard<std::mutex> lk(mu);
+  std::string n = std::string(base) + "[" + std::to_string(M) + "x" + std::to_string(N) + "x" + std::to_string(K) + "]";
+  return names.insert(n).first->c_str();
+}
+
 ProfScope::ProfScope(const char *name, cudaStream_t s, double flops, double bytes)
     : name_(name), s_(s), flops_(flops), bytes_(bytes) {
   if (!g_on) return;
-  cudaEventCreate(&a_);
-  cudaEventCreate(&b_);
+  a_ = take_event();
+  b_ = take_event();
   cudaEventRecord(a_, s_);
   active_ = true;
 }

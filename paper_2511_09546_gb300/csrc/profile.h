@@ -11,6 +11,9 @@ bool profiling();
 void profile_enable(bool on);
 bool profile_query(const char *name, uint64_t *count, double *ms, double *flops, double *bytes);
 std::string profile_names();
+// With IPEPS_PROF_SHAPES=1 in the environment, a persistent class name
+// "<base>[MxNxK]" per GEMM shape (shape histogram of a run); otherwise base.
+const char *shape_class(const char *base, int64_t M, int64_t N, int64_t K);
 
 // Records an event pair around the launches issued in its scope when
 // profiling is on; flops and bytes are the algorithmic work of the scope.

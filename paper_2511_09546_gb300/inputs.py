@@ -61,6 +61,17 @@ def product_state_cell(Lx: int, Ly: int, spinors, D: int = 1):
     return cell
 
 
+def perturbed_cells(cell, count: int, eps: float, seed: int):
+    """`count` copies of the unit cell, copy k with eps * U[-1, 1] added to every
+    entry (generator seeded by (seed, k)): the sequence of nearby tensors a
+    benchmark visits, as an optimiser's trial points do."""
+    out = []
+    for k in range(count):
+        rng = np.random.default_rng([seed, k])
+        out.append([[np.asarray(a) + eps * rng.uniform(-1.0, 1.0, np.shape(a)) for a in col] for col in cell])
+    return out
+
+
 def random_entries(n_total: int, count: int, seed: int):
     """Distinct flat indices for finite-difference probes."""
     rng = np.random.default_rng(seed)

@@ -67,6 +67,7 @@ def lib():
         L.ipeps_ham_create.argtypes = [i, dp, dp, dp, d, C.POINTER(vp)]
         L.ipeps_ham_heisenberg.argtypes = [i, d, C.POINTER(vp)]
         L.ipeps_ham_kitaev.argtypes = [d, C.POINTER(vp)]
+        L.ipeps_ham_j1j2.argtypes = [i, d, d, C.POINTER(vp)]
         L.ipeps_ham_set_nnn.argtypes = [vp, dp, dp]
         L.ipeps_ham_destroy.argtypes = [vp]
         L.ipeps_ctmrg.argtypes = [sp, vp, i, d, i, i, C.POINTER(vp), C.POINTER(i), dp, vp]
@@ -82,7 +83,8 @@ def lib():
         L.ipeps_gemm_noalloc.argtypes = [i, i, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
         L.ipeps_gemm_noalloc.restype = i
         L.ipeps_optimize.argtypes = [sp, vp, vp, C.POINTER(Opts), ITER_CB, vp, vp]
-        for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ham_set_nnn", "ipeps_ctmrg",
+        for name in ("ipeps_ham_create", "ipeps_ham_heisenberg", "ipeps_ham_kitaev", "ipeps_ham_set_nnn",
+                     "ipeps_ham_j1j2", "ipeps_ctmrg",
                      "ipeps_env_corner_spectra", "ipeps_energy", "ipeps_energy_grad",
                      "ipeps_precondition", "ipeps_optimize"):
             getattr(L, name).restype = i
@@ -162,8 +164,9 @@ def ham_set_nnn(ham, d1, d2):
 def ham_j1j2(J1=1.0, J2=0.5, rotated=True):
     """J1-J2 Heisenberg model: J1 S.S on nearest neighbours (sublattice-rotated
     when rotated), J2 S.S on both diagonals (never rotated: same sublattice)."""
-    ss = np.array([[0.25, 0, 0, 0], [0, -0.25, 0.5, 0], [0, 0.5, -0.25, 0], [0, 0, 0, 0.25]])
-    return ham_set_nnn(ham_heisenberg(rotated, J1), J2 * ss, J2 * ss)
+    out = C.c_void_p()
+    _check(lib().ipeps_ham_j1j2(int(rotated), J1, J2, C.byref(out)))
+    return Ham(out)
 
 
 def ham_kitaev(K=-1.0):
@@ -175,6 +178,7 @@ def ham_kitaev(K=-1.0):
 class Env:
     def __init__(self, handle, shape, chi):
         self.h, self.shape, self.chi = handle, shape, chi
+        self.version = 0  # advanced by every ctmrg() that updates this environment
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -199,6 +203,8 @@ def ctmrg(A, chi, tol=1e-10, maxit=500, prec=FP64, env=None, allow_unconverged=F
                            C.byref(it), C.byref(err), _stream())
     if env is None and h.value:
         env = Env(h, shape, chi)
+    elif env is not None:
+        env.version += 1
     _check(st, allow=(5,) if allow_unconverged else ())
     return env, it.value, err.value
 
@@ -334,3 +340,34 @@ def gemm_noalloc(A, B, C, ta=False, tb=False, alpha=1.0, beta=0.0):
     _check(lib().ipeps_gemm_noalloc(int(ta), int(tb), M, N, K, alpha, C_ptr(A), A.shape[1], C_ptr(B),
                                     B.shape[1], beta, C_ptr(C), C.shape[1], _stream()))
     return C
+
+
+class EnergyFunction(torch.autograd.Function):
+    """E(A) as a differentiable function: the forward runs CTMRG to its fixed
+    point (warm-started from `state["env"]` when present) and the energy; the
+    backward calls ipeps_energy_grad, the fixed-point gradient dE/dA of the
+    library, at the forward's environment."""
+
+    @staticmethod
+    def forward(ctx, A, ham, chi, tol, maxit, prec, state):
+        env, _, _ = ctmrg(A, chi, tol=tol, maxit=maxit, prec=prec, env=state.get("env"))
+        state["env"] = env
+        E = energy(A, env, ham)
+        ctx.save_for_backward(A)
+        ctx.env, ctx.version, ctx.ham = env, env.version, ham
+        return torch.tensor(E, dtype=torch.float64, device=A.device)
+
+    @staticmethod
+    def backward(ctx, gE):
+        (A,) = ctx.saved_tensors
+        if ctx.env.version != ctx.version:
+            raise RuntimeError("the environment of this energy was advanced by a later ctmrg() before backward")
+        _, g = energy_grad(A.detach(), ctx.env, ctx.ham)
+        return gE * g, None, None, None, None, None, None
+
+
+def energy_fn(A, ham, chi, tol=1e-10, maxit=500, prec=FP64, state=None):
+    """E(A) per site with autograd support (see EnergyFunction).  A: CUDA float64
+    tensor (Lx, Ly, d, D, D, D, D).  state: a dict that keeps the environment
+    between calls for warm starts (a fresh dict each call cold-starts)."""
+    return EnergyFunction.apply(A, ham, chi, tol, maxit, prec, {} if state is None else state)

@@ -1,0 +1,71 @@
+"""Writes the stored oracle values that the GPU tests compare with, for cases
+whose oracle run takes minutes (so that the GPU suite does not repeat it).
+Every number comes from oracle/ (FP64, CPU) on inputs from the seeded
+generators; nothing here calls the CUDA path.
+
+  python tests/golden/make_golden.py rangefinder   # D=4, chi=68 truncated-SVD case
+  python tests/golden/make_golden.py lbfgs         # plain (5) and preconditioned (3) L-BFGS iterations
+"""
+import json
+import os
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+from oracle import ctmrg as OC  # noqa: E402
+from oracle import gradient as OG  # noqa: E402
+from oracle import models as OM  # noqa: E402
+from oracle import optimize as OO  # noqa: E402
+from paper_2511_09546_gb300 import inputs  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _write(name, rec):
+    rec["threads"] = torch.get_num_threads()
+    with open(os.path.join(HERE, name), "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print("wrote", name, flush=True)
+
+
+def rangefinder():
+    """Heisenberg 1x1 (rotated), random D=4 tensor (uniform seed 3), chi=68: the
+    four-corner product is 1088 x 1088, beyond the size where the GPU path cold
+    starts its projector SVD from a random range finder."""
+    chi, seed, tol = 68, 3, 1e-11
+    cell = inputs.uniform_cell(1, 1, 2, 4, seed)
+    t0 = time.time()
+    E, g, info = OG.energy_and_gradient(cell, OM.heisenberg(True), chi, tol=tol, maxit=800, return_info=True)
+    gap = min(OC.cut_gaps(1, 1, OC.as_torch_cell(cell), info["env"], chi))
+    _write(f"rangefinder_d4_chi{chi}.json",
+           {"case": "uniform_cell(1, 1, 2, 4, seed=3), Heisenberg rotated", "chi": chi, "ctm_tol": tol, "E": E,
+            "grad": g[0][0].ravel().tolist(), "min_cut_gap": gap, "ctm_iters": info["ctm_iters"],
+            "adjoint_residual": info["adjoint_residual"], "seconds": time.time() - t0})
+
+
+def lbfgs():
+    """Oracle L-BFGS iterates at D=2, chi=16 from the seeded start of the
+    survey's first configuration: 5 plain iterations, 3 preconditioned."""
+    w = inputs.WORKLOADS["heis_d2_chi16"]
+    out = {}
+    for name, pre, iters in (("plain", False, 5), ("preconditioned", True, 3)):
+        t0 = time.time()
+        cell = w["gen"]()
+
+        def cb(rec):
+            print(name, rec, flush=True)
+
+        _, _, log = OO.optimize(cell, OM.heisenberg(True), w["chi"], precond=pre, maxiter=iters, tol=1e-11,
+                                ctm_maxit=150, callback=cb)
+        out[name] = {"iterations": iters, "log": [{k: (float(v) if k != "k" else int(v)) for k, v in r.items()}
+                                                  for r in log], "seconds": time.time() - t0}
+    _write("lbfgs_heis_d2_chi16.json", {"workload": "heis_d2_chi16", "ctm_tol": 1e-11, "ctm_maxit": 150, **out})
+
+
+if __name__ == "__main__":
+    {"rangefinder": rangefinder, "lbfgs": lbfgs}[sys.argv[1]]()

@@ -43,6 +43,23 @@ def test_central_finite_differences(cfg1):
         assert abs(fd - g[0][0].ravel()[i]) < 2e-8, (i, fd, g[0][0].ravel()[i])
 
 
+def test_central_differences_every_entry(cfg1):
+    # all 32 entries of the D=2 tensor (the survey's cfg1 pin), step 1e-6
+    cell, ham, _, g, info = cfg1
+    A = cell[0][0]
+    h = 1e-6
+    fd = np.zeros(A.size)
+    for i in range(A.size):
+        vals = []
+        for sgn in (1, -1):
+            Ap = A.copy().ravel()
+            Ap[i] += sgn * h
+            E, _ = G.energy_at([[Ap.reshape(A.shape)]], ham, 16, tol=1e-12, maxit=400, env=info["env"])
+            vals.append(E)
+        fd[i] = (vals[0] - vals[1]) / (2 * h)
+    assert np.max(np.abs(fd - g[0][0].ravel())) < 2e-8
+
+
 def test_product_state_gradient_vanishes():
     # D=1 real spinors all have E = -1/2 in the rotated frame: g = 0
     cell = inputs.product_state_cell(1, 1, [[0.8, -0.35]])
