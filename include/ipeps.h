@@ -62,12 +62,24 @@ typedef enum {
                            spectra change < 1e-6 (or stops improving), then FP64
                            iterations until tol: the fixed point, energy and
                            gradient are those of the FP64 path. */
-  IPEPS_TF32X3_ALL = 2  /* throughput mode for large chi D^2: every bulk GEMM,
+  IPEPS_TF32X3_ALL = 2, /* throughput mode for large chi D^2: every bulk GEMM,
                            the four-corner and projector products included, and
                            the adjoint's GEMMs as 3xTF32; SVD, normalisation and
                            preconditioner FP64; no FP64 phase, so the spectra
                            change stalls near the 3xTF32 noise floor and a tol
                            below it ends in IPEPS_ERR_NOT_CONVERGED */
+  IPEPS_FP64_TC = 3,    /* FP64-grade results from the BF16 tensor cores: every
+                           GEMM large enough to gain (contractions, SVD and
+                           adjoint products, metric) is formed from 8 exponent-
+                           aligned 7-bit digits per operand, 36 BF16 products
+                           per term summed exactly in FP32 chunks and in 64-bit
+                           fixed point (error bound of an FP64 GEMM taken relative
+                           to the row and column maxima); small GEMMs, SVD
+                           rotations, reductions and GMRES stay FP64 */
+  IPEPS_BF16X3 = 4      /* BF16x3 contractions: the bulk GEMMs from 2 digits per
+                           operand (3 BF16 products per term, about 2^-15 of the
+                           row and column maxima), the four-corner and projector
+                           products and every other GEMM as IPEPS_FP64_TC */
 } ipeps_prec;
 
 typedef struct {
@@ -203,7 +215,9 @@ ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham h
 /* The contraction engine's GEMM (row-major): C = alpha op(A) op(B) + beta C,
  * op(A) M x K (ta != 0: A stored K x M), op(B) K x N (tb != 0: B stored
  * N x K), device pointers, leading dimensions in elements.  prec selects the
- * FP64 CUDA-core kernels or the 3xTF32 tcgen05 kernel (FP32 accumulate).
+ * FP64 CUDA-core kernels, the 3xTF32 tcgen05 kernel (FP32 accumulate;
+ * IPEPS_TF32X3 and IPEPS_TF32X3_ALL alike) or the BF16-digit tcgen05 kernel
+ * (IPEPS_FP64_TC: 8 digits, IPEPS_BF16X3: 2 digits).
  * Every contraction of the hot path lowers to this call (after at most one
  * permutation per operand). */
 ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,

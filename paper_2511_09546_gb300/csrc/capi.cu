@@ -255,7 +255,8 @@ ipeps_status ipeps_ctmrg(const ipeps_shape *shape, const double *A_dev, int chi,
     IPEPS_REQUIRE(A_dev && inout_env, "ctmrg: NULL argument");
     IPEPS_REQUIRE(chi >= 1 && chi <= 4096, "ctmrg: chi out of range");
     IPEPS_REQUIRE(maxit >= 0 && tol >= 0.0, "ctmrg: bad tol / maxit");
-    IPEPS_REQUIRE(prec == IPEPS_FP64 || prec == IPEPS_TF32X3 || prec == IPEPS_TF32X3_ALL, "ctmrg: unknown precision");
+    IPEPS_REQUIRE(prec >= IPEPS_FP64 && prec <= IPEPS_BF16X3, "ctmrg: unknown precision");
+    ipeps::PolicyScope policy(ipeps::fp64_grade_of(ipeps::Prec(prec)));
     check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
     std::unique_ptr<ipeps_env_s> fresh;
     ipeps_env env = *inout_env;
@@ -274,6 +275,7 @@ ipeps_status ipeps_ctmrg(const ipeps_shape *shape, const double *A_dev, int chi,
     double err = 0.0;
     int it = 0;
     if (maxit > 0) it = ipeps::ctmrg_run(env->impl, A_dev, tol, maxit, ipeps::Prec(prec), &err, s);
+    ipeps::tc_check_errors(s);
     if (iters_out) *iters_out = it;
     if (err_out) *err_out = err;
     if (fresh) *inout_env = fresh.release();
@@ -314,7 +316,9 @@ ipeps_status ipeps_energy(const ipeps_shape *shape, const double *A_dev, ipeps_e
     IPEPS_REQUIRE(A_dev && ham && E_out, "energy: NULL argument");
     check_env(env, c);
     IPEPS_REQUIRE(ham->impl.d == c.d, "energy: Hamiltonian has a different d");
+    ipeps::PolicyScope policy(ipeps::fp64_grade_of(env->impl.prec));
     *E_out = ipeps::energy_only(c, A_dev, env->impl, ham->impl, s);
+    ipeps::tc_check_errors(s);
     if (!std::isfinite(*E_out)) throw ipeps::Error(IPEPS_ERR_NONFINITE, "energy is not finite");
     return IPEPS_OK;
   });
@@ -331,7 +335,9 @@ ipeps_status ipeps_energy_grad(const ipeps_shape *shape, const double *A_dev, ip
     check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
     double ares = 0.0, fpres = 0.0;
     int amv = 0;
+    ipeps::PolicyScope policy(ipeps::fp64_grade_of(env->impl.prec));
     *E_out = ipeps::energy_grad(c, A_dev, env->impl, ham->impl, grad_dev, s, &ares, &amv, &fpres);
+    ipeps::tc_check_errors(s);
     if (!std::isfinite(*E_out)) throw ipeps::Error(IPEPS_ERR_NONFINITE, "energy is not finite");
     if (!(ares < 1e-8)) {
       g_last_error = "adjoint solve did not converge (relative residual " + std::to_string(ares) + ")";
@@ -363,7 +369,9 @@ ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, i
       IPEPS_CUDA(cudaStreamSynchronize(s));
       delta = std::max(h * h, 1e-12);
     }
+    ipeps::PolicyScope policy(ipeps::fp64_grade_of(env->impl.prec));
     double r = ipeps::precondition_all(env->impl, A_dev, g_dev, delta, krylov, restarts, out_dev, s);
+    ipeps::tc_check_errors(s);
     IPEPS_CUDA(cudaStreamSynchronize(s));
     if (resid_out) *resid_out = r;
     return IPEPS_OK;
@@ -380,10 +388,14 @@ ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, i
     IPEPS_REQUIRE(C || M * N == 0, "gemm: NULL output");
     IPEPS_REQUIRE((lda >= (ta ? M : K) && ldb >= (tb ? K : N)) || K == 0, "gemm: leading dimension too small");
     IPEPS_REQUIRE(ldc >= N, "gemm: leading dimension of C too small");
+    ipeps::PolicyScope policy(ipeps::Prec::FP64);
     if (prec == IPEPS_TF32X3 || prec == IPEPS_TF32X3_ALL) ipeps::gemm_tf32x3(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     else if (prec == IPEPS_FP64) ipeps::gemm_f64(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    else if (prec == IPEPS_FP64_TC) ipeps::gemm_oz(8, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
+    else if (prec == IPEPS_BF16X3) ipeps::gemm_oz(2, ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
     else throw ipeps::Error(IPEPS_ERR_ARG, "gemm: unknown precision");
     IPEPS_CUDA(cudaStreamSynchronize(s));
+    ipeps::tc_check_errors(s);
     return IPEPS_OK;
   });
 }
@@ -429,11 +441,14 @@ ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham h
     IPEPS_REQUIRE(A_dev && ham && opts, "optimize: NULL argument");
     IPEPS_REQUIRE(opts->chi >= 1 && opts->ctm_maxit >= 1 && opts->history >= 0 && opts->maxiter >= 0 &&
                       opts->krylov >= 1 && opts->restarts >= 1 && opts->prec >= IPEPS_FP64 &&
-                      opts->prec <= IPEPS_TF32X3_ALL,
+                      opts->prec <= IPEPS_BF16X3,
                   "optimize: bad options");
     IPEPS_REQUIRE(ham->impl.d == c.d, "optimize: Hamiltonian has a different d");
     check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");
-    return ipeps::optimize_impl(c, A_dev, ham->impl, *opts, cb, user, s);
+    ipeps::PolicyScope policy(ipeps::fp64_grade_of(ipeps::Prec(opts->prec)));
+    ipeps_status st = ipeps::optimize_impl(c, A_dev, ham->impl, *opts, cb, user, s);
+    ipeps::tc_check_errors(s);
+    return st;
   });
 }
 

@@ -95,8 +95,14 @@ void contract(const Ten &A, const std::string &la, const Ten &B, const std::stri
     Cp = Cb.p;
   }
   double ga = direct ? alpha : 1.0, gb = direct ? beta : 0.0;
-  if (prec != Prec::FP64 && tc_worthwhile(m, n, k)) gemm_tf32x3(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
-  else gemm_f64(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
+  if ((prec == Prec::TF32X3 || prec == Prec::TF32X3_ALL) && tc_worthwhile(m, n, k))
+    gemm_tf32x3(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
+  else if (prec == Prec::BF16X3 && oz_worthwhile(m, n, k))
+    gemm_oz(2, ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
+  else if (prec == Prec::FP64_TC && oz_worthwhile(m, n, k))
+    gemm_oz(8, ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
+  else
+    gemm_f64(ta, tb, m, n, k, ga, Ap, lda, Bp, ldb, gb, Cp, n, s);
   if (!direct) permute(Cp, dims_of(FA + FB), perm_to(FA + FB, lc), C.p, s, alpha, beta);
 }
 

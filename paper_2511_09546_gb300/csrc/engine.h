@@ -21,7 +21,31 @@
 
 namespace ipeps {
 
-enum class Prec { FP64 = 0, TF32X3 = 1, TF32X3_ALL = 2 };
+enum class Prec { FP64 = 0, TF32X3 = 1, TF32X3_ALL = 2, FP64_TC = 3, BF16X3 = 4 };
+
+// Arithmetic of the FP64-grade GEMMs (gemm_f64) issued by this thread: the
+// CUDA-core DFMA kernels (Prec::FP64) or, for Prec::FP64_TC, the
+// exponent-aligned BF16-slice tensor-core GEMM with 8 digits where the shape
+// is large enough.  Set for the duration of a C-ABI call by PolicyScope.
+Prec &fp64_policy();
+struct PolicyScope {
+  Prec old;
+  explicit PolicyScope(Prec p) : old(fp64_policy()) { fp64_policy() = p; }
+  ~PolicyScope() { fp64_policy() = old; }
+  PolicyScope(const PolicyScope &) = delete;
+  PolicyScope &operator=(const PolicyScope &) = delete;
+};
+// FP64-grade products for contractions run in precision p
+inline Prec fp64_grade_of(Prec p) { return (p == Prec::FP64_TC || p == Prec::BF16X3) ? Prec::FP64_TC : Prec::FP64; }
+// the shape is large enough for the slice GEMM to beat the DFMA kernels
+bool oz_worthwhile(int64_t m, int64_t n, int64_t k);
+// C = alpha op(A) op(B) + beta C on the BF16 tensor cores with `slices` 7-bit
+// digits per operand (2: BF16x3, 3, or 8: FP64-grade); row-major, FP64 in and out
+void gemm_oz(int slices, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+             int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s);
+// error word of the tensor-core kernels and its check (synchronises s)
+int *tc_error_word();
+void tc_check_errors(cudaStream_t s);
 
 struct Ten {
   double *p = nullptr;

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "common.h"
+#include "engine.h"
 #include "kernels.h"
 #include "profile.h"
 
@@ -153,10 +154,27 @@ int num_sms() {
 }
 }  // namespace
 
+Prec &fp64_policy() {
+  static thread_local Prec p = Prec::FP64;
+  return p;
+}
+
+// The slice GEMM packs both operands (4 launches) and pads M to 128 and N to
+// 64; below about 2^24 multiply-adds, or for very thin outputs, the DFMA
+// kernels finish first.
+bool oz_worthwhile(int64_t m, int64_t n, int64_t k) {
+  return m >= 32 && n >= 16 && k >= 64 && double(m) * n * k >= double(1 << 24);
+}
+
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
               int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc,
               cudaStream_t s, int64_t batch, int64_t sA, int64_t sB, int64_t sC) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
+  if (fp64_policy() == Prec::FP64_TC && K > 0 && oz_worthwhile(M, N, K)) {
+    for (int64_t b = 0; b < batch; ++b)
+      gemm_oz(8, ta, tb, M, N, K, alpha, A + b * sA, lda, B + b * sB, ldb, beta, C + b * sC, ldc, s);
+    return;
+  }
   if (K <= 0) {
     // C = beta C
     for (int64_t b = 0; b < batch; ++b) {

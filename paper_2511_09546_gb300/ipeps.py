@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "libipeps.so")
 _lib = None
 
-FP64, TF32X3, TF32X3_ALL = 0, 1, 2
+FP64, TF32X3, TF32X3_ALL, FP64_TC, BF16X3 = 0, 1, 2, 3, 4
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_NOMEM", 3: "ERR_CUDA", 4: "ERR_NONFINITE",
           5: "ERR_NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_CANCELLED"}
 
