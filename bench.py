@@ -172,8 +172,12 @@ def _ham(ipeps, w):
     return ipeps.ham_heisenberg(True) if w["d"] == 2 else ipeps.ham_kitaev(-1.0)
 
 
+PRECS = ["fp64", "tf32x3", "tf32x3_all", "fp64_tc", "bf16x3"]
+
+
 def _prec(ipeps, name):
-    return {"fp64": ipeps.FP64, "tf32x3": ipeps.TF32X3, "tf32x3_all": ipeps.TF32X3_ALL}[name]
+    return {"fp64": ipeps.FP64, "tf32x3": ipeps.TF32X3, "tf32x3_all": ipeps.TF32X3_ALL, "fp64_tc": ipeps.FP64_TC,
+            "bf16x3": ipeps.BF16X3}[name]
 
 
 def roofline(prof, peaks_live):
@@ -186,9 +190,18 @@ def roofline(prof, peaks_live):
     peaks = _peaks()
     total = sum(v["ms"] for v in prof.values())
     if dom == "tc_gemm":
-        roof = {"kernel": dom, "bound": "tensor", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
+        roof = {"kernel": dom, "bound": "tensor", "achieved": 3 * st["flops"] / (st["ms"] * 1e-3) / 1e12,
                 "peak": peaks_live.get("tf32_tflops"), "unit": "TFLOP/s",
-                "peak_source": "measured: cuBLAS TF32 GEMM 8192^3 on this GPU (torch.matmul, best of 3)"}
+                "peak_source": "measured: cuBLAS TF32 GEMM 8192^3 on this GPU (torch.matmul, best of 3)",
+                "note": "achieved = issued TF32 FLOP/s (3 products per term)"}
+    elif dom.startswith("oz") and dom.endswith("_gemm"):
+        digits = int(dom[2:-5])
+        products = digits * (digits + 1) // 2
+        roof = {"kernel": dom, "bound": "tensor", "achieved": products * st["flops"] / (st["ms"] * 1e-3) / 1e12,
+                "peak": peaks.get("bf16_tflops_sustained", 1705.9), "unit": "TFLOP/s",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                "note": f"achieved = issued BF16 FLOP/s ({products} digit products per FP64 term); "
+                        f"FP64-equivalent {st['flops'] / (st['ms'] * 1e-3) / 1e12:.2f} TFLOP/s"}
     elif st["flops"] > 0:
         roof = {"kernel": dom, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
                 "peak": peaks_live.get("fp64_tflops"), "unit": "TFLOP/s",
@@ -306,7 +319,8 @@ def run_ours(args, rank, world, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == ipeps.FP64 else "tf32x3+f64",
+        "dtype": {ipeps.FP64: "f64", ipeps.FP64_TC: "f64 from bf16 digits (tensor cores, fp32/int64 accumulate)",
+                  ipeps.BF16X3: "bf16x3+f64", ipeps.TF32X3: "tf32x3+f64", ipeps.TF32X3_ALL: "tf32x3"}[prec],
         "data": "synthetic",
         "config": {"workload": args.workload + (": Heisenberg square lattice 1x1, d=2, D=4, chi=64, Neel-like D=1 "
                                                 "seed in D=4 + 1e-2 noise (seed 0)" if args.workload == "heis_d4_chi64"
@@ -543,8 +557,9 @@ def run_ttt(args):
 
 
 def run_gemm(args):
-    """--mode gemm: the 3xTF32 tcgen05 GEMM on n x n x n FP64 operands, timed per
-    kernel class with CUDA events (W warm-up calls, K timed calls)."""
+    """--mode gemm: one tensor-core GEMM (3xTF32, or the BF16-digit kernel for
+    --prec fp64_tc / bf16x3) on n x n x n FP64 operands, timed per kernel class
+    with CUDA events (W warm-up calls, K timed calls)."""
     import torch
 
     import __graft_entry__ as entry
@@ -557,7 +572,8 @@ def run_gemm(args):
     A = torch.randn((n, n), generator=g, dtype=torch.float64).cuda()
     B = torch.randn((n, n), generator=g, dtype=torch.float64).cuda()
     C = torch.zeros((n, n), dtype=torch.float64, device="cuda")
-    prec = _prec(ipeps, args.prec if args.prec != "fp64" else "tf32x3")
+    name = args.prec if args.prec != "fp64" else "tf32x3"
+    prec = _prec(ipeps, name)
     for _ in range(args.warmup):
         ipeps.gemm(A, B, C=C, prec=prec)
     torch.cuda.synchronize()
@@ -570,13 +586,19 @@ def run_gemm(args):
     ipeps.profile(False)
     ref_rows = A[:64] @ B
     err = float((C[:64] - ref_rows).abs().max() / ref_rows.abs().max())
-    tf32_peak = peaks_live["tf32_tflops"]
-    gm, pk = st.get("tc_gemm", {}), st.get("tc_pack", {})
+    if name.startswith("tf32"):
+        kern, pack, products, peak, unit = "tc_gemm", "tc_pack", 3, peaks_live["tf32_tflops"], "tf32"
+    else:
+        digits = 8 if name == "fp64_tc" else 2
+        kern, pack = f"oz{digits}_gemm", "oz_pack"
+        products = digits * (digits + 1) // 2
+        peak, unit = _peaks().get("bf16_tflops", 1908.5), "bf16"
+    gm, pk = st.get(kern, {}), st.get(pack, {})
     logical = gm["flops"] / (gm["ms"] * 1e-3) / 1e12
-    rec = {"mode": "gemm", "n": n, "launches": gm.get("count"), "gemm_ms": gm["ms"] / max(1, gm["count"]),
+    rec = {"mode": "gemm", "prec": name, "n": n, "launches": gm.get("count"), "gemm_ms": gm["ms"] / max(1, gm["count"]),
            "pack_ms": pk.get("ms", 0.0) / max(1, pk.get("count", 1)),
-           "logical_tflops": logical, "issued_tf32_tflops": 3 * logical,
-           "tf32_peak_tflops": tf32_peak, "issued_frac_of_tf32_peak": 3 * logical / tf32_peak,
+           "logical_tflops": logical, "products_per_term": products, f"issued_{unit}_tflops": products * logical,
+           f"{unit}_peak_tflops": peak, "issued_frac_of_peak": products * logical / peak,
            "pack_gbs": pk.get("bytes", 0.0) / max(1e-9, pk.get("ms", 0.0) * 1e-3) / 1e9,
            "rel_err_vs_fp64": err, "peaks_live": peaks_live}
     print(json.dumps(rec), flush=True)
@@ -588,7 +610,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "tf32x3", "tf32x3_all"])
+    ap.add_argument("--prec", default="fp64", choices=PRECS)
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="pass", choices=["pass", "optimize", "gemm", "ctmrg", "ttt"])

@@ -41,8 +41,18 @@ inline Prec fp64_grade_of(Prec p) { return (p == Prec::FP64_TC || p == Prec::BF1
 bool oz_worthwhile(int64_t m, int64_t n, int64_t k);
 // C = alpha op(A) op(B) + beta C on the BF16 tensor cores with `slices` 7-bit
 // digits per operand (2: BF16x3, 3, or 8: FP64-grade); row-major, FP64 in and out
+struct OzPacked;
 void gemm_oz(int slices, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
-             int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s);
+             int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s,
+             const OzPacked *packed_a = nullptr);
+// A left operand that several FP64-grade products share, packed once into
+// digits (nullptr when the FP64 policy is the DFMA path); gemm_f64_packed uses
+// the packed digits when the shape takes the tensor-core path and A otherwise
+std::shared_ptr<OzPacked> pack_left_fp64(bool ta, int64_t M, int64_t K, const double *A, int64_t lda,
+                                         cudaStream_t s);
+void gemm_f64_packed(const OzPacked *pa, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                     const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                     int64_t ldc, cudaStream_t s);
 // error word of the tensor-core kernels and its check (synchronises s)
 int *tc_error_word();
 void tc_check_errors(cudaStream_t s);

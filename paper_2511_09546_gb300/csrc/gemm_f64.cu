@@ -89,8 +89,9 @@ __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M,
     }
   }
 }
-// Small output (M N <= 1024), long K: block z takes a K slice, each warp a set
-// of outputs, lanes stride over k; partial sums go to W[z] (reduced below).
+// Small output (M N <= 1024), long K: block (z, y) takes K slice z and the 8
+// outputs 8 y .. 8 y + 7, one per warp, lanes stride over k; partial sums go
+// to W[z] (reduced below).
 __global__ void __launch_bounds__(256) multidot_kernel(bool ta, bool tb, int64_t M, int64_t N, int64_t K,
                                                        double alpha, const double *__restrict__ A, int64_t lda,
                                                        const double *__restrict__ B, int64_t ldb,
@@ -98,7 +99,9 @@ __global__ void __launch_bounds__(256) multidot_kernel(bool ta, bool tb, int64_t
   const int64_t z = blockIdx.x;
   const int64_t kbeg = z * kchunk, kend = kbeg + kchunk < K ? kbeg + kchunk : K;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t o = warp; o < M * N; o += 8) {
+  {
+    const int64_t o = int64_t(blockIdx.y) * 8 + warp;
+    if (o >= M * N) return;
     const int64_t m = o / N, n = o % N;
     double acc = 0.0;
     for (int64_t k = kbeg + lane; k < kend; k += 32) {
@@ -159,11 +162,10 @@ Prec &fp64_policy() {
   return p;
 }
 
-// The slice GEMM packs both operands (4 launches) and pads M to 128 and N to
-// 64; below about 2^24 multiply-adds, or for very thin outputs, the DFMA
-// kernels finish first.
+// The slice GEMM packs both operands (4 launches) and pads M to 128, N to 64
+// and K to 64; below about 2^23 multiply-adds the DFMA kernels finish first.
 bool oz_worthwhile(int64_t m, int64_t n, int64_t k) {
-  return m >= 32 && n >= 16 && k >= 64 && double(m) * n * k >= double(1 << 24);
+  return m >= 16 && n >= 8 && k >= 16 && double(m) * n * k >= double(1 << 23);
 }
 
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
@@ -194,11 +196,13 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
   const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
   const int sms = num_sms();
   if (batch == 1 && M * N <= 1024 && K >= 256) {
-    int64_t S = std::min<int64_t>(4 * sms, (K + 255) / 256);
+    const int64_t groups = (M * N + 7) / 8;
+    int64_t S = std::max<int64_t>(1, std::min<int64_t>((4 * sms + groups - 1) / groups, (K + 127) / 128));
     int64_t kchunk = (K + S - 1) / S;
     S = (K + kchunk - 1) / kchunk;
     double *W = static_cast<double *>(dev_alloc(size_t(S) * M * N * sizeof(double), s));
-    multidot_kernel<<<unsigned(S), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, W, kchunk);
+    multidot_kernel<<<dim3(unsigned(S), unsigned((M * N + 7) / 8)), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B,
+                                                                                   ldb, W, kchunk);
     int rg = int(std::min<int64_t>((M * N + 255) / 256, 4 * sms));
     splitk_reduce<<<rg, 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
     count_launch(2);
@@ -309,7 +313,8 @@ void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double 
     int64_t S = std::min<int64_t>({int64_t(4) * sms, (K + 255) / 256, fit});
     int64_t kchunk = (K + S - 1) / S;
     S = (K + kchunk - 1) / kchunk;
-    multidot_kernel<<<unsigned(S), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, W, kchunk);
+    multidot_kernel<<<dim3(unsigned(S), unsigned((M * N + 7) / 8)), 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B,
+                                                                                   ldb, W, kchunk);
     splitk_reduce<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
     count_launch(2);
     check_launch("gemm_noalloc multidot");

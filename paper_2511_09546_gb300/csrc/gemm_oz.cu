@@ -8,8 +8,8 @@
 //
 //   Row i of op(A) is scaled by 2^-E_i with 2^E_i > max_k |a_ik| and written as
 //   S digits of 7 bits, a_ik = 2^(E_i - 7) sum_p a~_ikp with a~_ikp = d_p 2^(-7p),
-//   d_0 in [-128, 128] and d_p in [-64, 64] for p >= 1 (each digit the rounded
-//   remainder of the previous ones; FP64 arithmetic, exact).  Columns of op(B)
+//   d_0 in [-128, 128] and d_p in [-64, 63] for p >= 1 (the balanced base-128
+//   digits of the integer round(a_ik 2^(7S - E_i))).  Columns of op(B)
 //   likewise (exponent F_j).  Every digit is an integer of at most 8 bits times
 //   a power of two, hence exact in BF16.
 //
@@ -51,6 +51,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <memory>
 #include <string>
 
 #include "common.h"
@@ -89,12 +90,20 @@ template <int S, int BN> __host__ __device__ constexpr int ostages() {
   return ORING / stage_bytes<S, BN>() < 8 ? ORING / stage_bytes<S, BN>() : 8;
 }
 
+// E with 2^E > x for the largest |x| of a row given by its bit pattern (0 for zero)
+__device__ __forceinline__ int oz_exp(unsigned long long bits) {
+  int e = 0;
+  frexp(__longlong_as_double((long long)bits), &e);
+  return e;
+}
+
 // A~ in slice kt, digit p: rows m0.., columns p Kp + kt OBK (the packed operand is
 // rows x S Kp with digit p in columns p Kp .. p Kp + Kp - 1)
 template <int S, int BN>
 __global__ void __launch_bounds__(othreads<BN>(), 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                   const int *__restrict__ ea, const int *__restrict__ eb, int64_t M, int64_t N, int Kp,
+                   const unsigned long long *__restrict__ ma_x, const unsigned long long *__restrict__ mb_x,
+                   int64_t M, int64_t N, int Kp,
                    int nk, int kper, double alpha, double beta, double *__restrict__ C, int64_t ldc,
                    int64_t zstride, int *err) {
   static_assert(tmem_cols<S, BN>() <= 512, "accumulators exceed tensor memory");
@@ -255,14 +264,14 @@ __global__ void __launch_bounds__(othreads<BN>(), 1)
       const int64_t row = m0 + (warp & 3) * 32 + lane;
       const int64_t col0 = n0 + (warp >> 2) * 32;
       if (row < M) {
-        const int er = ea[row];
+        const int er = oz_exp(ma_x[row]);
         double *crow = C + blockIdx.z * zstride + row * ldc + col0;
         const double fix = ldexp(1.0, -OBETA * (LEX - 1));
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           if (col0 + j < N) {
             const double t = double(acc[j]) * fix + double(tail[j]);
-            const double v = alpha * ldexp(t, er + eb[col0 + j] - 2 * OBETA);
+            const double v = alpha * ldexp(t, er + oz_exp(mb_x[col0 + j]) - 2 * OBETA);
             crow[j] = (beta == 0.0) ? v : v + beta * crow[j];
           }
         }
@@ -282,54 +291,70 @@ __global__ void __launch_bounds__(othreads<BN>(), 1)
   }
 }
 
-// exponent E_r with 2^E_r > max_k |op(X)[r, k]| (0 for a zero row), one row of
-// op(X) per warp when its elements are contiguous
-__global__ void oz_rowexp_contig(const double *__restrict__ X, int64_t ld, int64_t rows, int64_t K, int *ex,
-                                 int64_t rows_pad) {
-  const int64_t r = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (r >= rows_pad) return;
-  double m = 0.0;
-  if (r < rows)
-    for (int64_t k = lane; k < K; k += 32) m = fmax(m, fabs(X[r * ld + k]));
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) {
-    int e = 0;
-    frexp(m, &e);
-    ex[r] = e;
+// Operand packing.  A row r of op(X) (row r of A, or column r of B) is
+// scaled by 2^-E_r with 2^E_r > max_k |op(X)[r, k]|, taken from the largest bit
+// pattern of |x| in the row (the IEEE order of non-negative doubles is the
+// order of their bit patterns).  Both kernels walk 32 x 64 tiles of op(X) (32
+// rows, 64 K elements) read along whichever index is contiguous in memory.
+
+__device__ __forceinline__ double oz_load(const double *__restrict__ X, int64_t ld, bool trans, int64_t rows,
+                                          int64_t K, int64_t r, int64_t k) {
+  return (r < rows && k < K) ? (trans ? X[k * ld + r] : X[r * ld + k]) : 0.0;
+}
+
+// mx[r] = max over the tile's k of the bit pattern of |op(X)[r, k]| (atomic max
+// across tiles; mx zeroed beforehand)
+__global__ void __launch_bounds__(256) oz_absmax_kernel(const double *__restrict__ X, int64_t ld, bool trans,
+                                                        int64_t rows, int64_t K,
+                                                        unsigned long long *__restrict__ mx) {
+  __shared__ unsigned long long part[8][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t k0 = int64_t(blockIdx.x) * 64, r0 = int64_t(blockIdx.y) * 32;
+  if (!trans) {
+    // warp ty: rows ty, ty + 8, ..; lanes along k (contiguous)
+    for (int i = ty; i < 32; i += 8) {
+      const int64_t r = r0 + i;
+      unsigned long long m = 0;
+      for (int j = tx; j < 64; j += 32)
+        m = max(m, (unsigned long long)__double_as_longlong(fabs(oz_load(X, ld, false, rows, K, r, k0 + j))));
+      for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (tx == 0 && r < rows && m) atomicMax(mx + r, m);
+    }
+  } else {
+    // lanes along r (contiguous), warp ty takes k = ty, ty + 8, ..
+    unsigned long long m = 0;
+    for (int j = ty; j < 64; j += 8)
+      m = max(m, (unsigned long long)__double_as_longlong(fabs(oz_load(X, ld, true, rows, K, r0 + tx, k0 + j))));
+    part[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0) {
+      for (int w = 1; w < 8; ++w) m = max(m, part[w][tx]);
+      if (r0 + tx < rows && m) atomicMax(mx + r0 + tx, m);
+    }
   }
 }
 
-// the same when the elements of a row of op(X) are strided (X stored K x rows)
-__global__ void oz_rowexp_strided(const double *__restrict__ X, int64_t ld, int64_t rows, int64_t K, int *ex,
-                                  int64_t rows_pad) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r >= rows_pad) return;
-  double m = 0.0;
-  if (r < rows)
-    for (int64_t k = 0; k < K; ++k) m = fmax(m, fabs(X[k * ld + r]));
-  int e = 0;
-  frexp(m, &e);
-  ex[r] = e;
-}
-
-// P[r][p Kp + k] = BF16 digit p of op(X)[r, k] 2^-E_r (zero outside rows x K),
-// one 256-thread block per 32 x 32 tile with a shared-memory transpose
+// P[r][p Kp + k] = digit p of op(X)[r, k]: F = round(x 2^(7S - E_r)) (|F| < 2^(7S),
+// 64-bit integer), split into balanced base-128 digits from the bottom
+// (d_p in [-64, 63] for p >= 1, the top digit d_0 in [-128, 128]), each stored as
+// the BF16 value d_p 2^(-7p).  Two consecutive k per thread: 32-bit stores,
+// 128 contiguous bytes per warp and digit.
 template <int S>
 __global__ void __launch_bounds__(256) oz_digits_kernel(const double *__restrict__ X, int64_t ld, bool trans,
                                                         int64_t rows, int64_t K, int64_t Kp,
-                                                        const int *__restrict__ ex, __nv_bfloat16 *__restrict__ P) {
-  __shared__ double T[32][33];  // T[k][r]
+                                                        const unsigned long long *__restrict__ mx,
+                                                        __nv_bfloat16 *__restrict__ P) {
+  __shared__ double T[64][33];  // T[k][r]
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-  const int64_t k0 = int64_t(blockIdx.x) * 32, r0 = int64_t(blockIdx.y) * 32;
+  const int64_t k0 = int64_t(blockIdx.x) * 64, r0 = int64_t(blockIdx.y) * 32;
+  if (trans) {
 #pragma unroll
-  for (int i = 0; i < 32; i += 8) {
-    if (trans) {
-      const int64_t k = k0 + ty + i, r = r0 + tx;
-      T[ty + i][tx] = (k < K && r < rows) ? X[k * ld + r] : 0.0;
-    } else {
-      const int64_t r = r0 + ty + i, k = k0 + tx;
-      T[tx][ty + i] = (k < K && r < rows) ? X[r * ld + k] : 0.0;
+    for (int i = 0; i < 64; i += 8) T[ty + i][tx] = oz_load(X, ld, true, rows, K, r0 + tx, k0 + ty + i);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 32; i += 8) {
+      T[tx][ty + i] = oz_load(X, ld, false, rows, K, r0 + ty + i, k0 + tx);
+      T[tx + 32][ty + i] = oz_load(X, ld, false, rows, K, r0 + ty + i, k0 + tx + 32);
     }
   }
   __syncthreads();
@@ -337,13 +362,28 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const double *__restrict
   for (int i = 0; i < 32; i += 8) {
     const int r = ty + i;
     const int64_t row = r0 + r;
-    double v = ldexp(T[tx][r], -ex[row] + OBETA);  // in (-2^7, 2^7): exact power-of-two scaling
-    __nv_bfloat16 *dst = P + row * (S * Kp) + k0 + tx;
+    const int sh = OBETA * S - oz_exp(mx[row]);
+    long long F[2];
+    F[0] = llrint(ldexp(T[2 * tx][r], sh));
+    F[1] = llrint(ldexp(T[2 * tx + 1][r], sh));
+    int d[2][S];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int p = S - 1; p >= 1; --p) {
+        const int v = int(((F[h] + 64) & 127) - 64);
+        d[h][p] = v;
+        F[h] = (F[h] - v) >> OBETA;
+      }
+      d[h][0] = int(F[h]);
+    }
+    uint32_t *dst = reinterpret_cast<uint32_t *>(P + row * (S * Kp) + k0) + tx;
 #pragma unroll
     for (int p = 0; p < S; ++p) {
-      const double d = rint(v);
-      v = (v - d) * double(1 << OBETA);  // exact: |v - d| <= 1/2
-      dst[p * Kp] = __float2bfloat16_rn(ldexpf(float(d), -OBETA * p));
+      const float sc = __int_as_float((127 - OBETA * p) << 23);  // 2^(-7p)
+      const __nv_bfloat16 lo = __float2bfloat16_rn(float(d[0][p]) * sc);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(float(d[1][p]) * sc);
+      dst[(p * Kp) / 2] = uint32_t(__bfloat16_as_ushort(lo)) | (uint32_t(__bfloat16_as_ushort(hi)) << 16);
     }
   }
 }
@@ -397,32 +437,57 @@ int oz_sms() {
   return sms;
 }
 
-template <int S, int BN>
-void oz_run(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
-            const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s) {
-  const int64_t Kp = (K + OBK - 1) / OBK * OBK;
-  const int64_t Mp = (M + OBM - 1) / OBM * OBM, Np = (N + BN - 1) / BN * BN;
-  IPEPS_REQUIRE(Mp / OBM <= 65535 && S * Kp <= 2147483647 && Kp / OBK <= (int64_t(1) << 24),
-                "oz_gemm: problem too large");
-  __nv_bfloat16 *Pa = static_cast<__nv_bfloat16 *>(dev_alloc(size_t(Mp) * S * Kp * 2, s));
-  __nv_bfloat16 *Pb = static_cast<__nv_bfloat16 *>(dev_alloc(size_t(Np) * S * Kp * 2, s));
-  int *ea = static_cast<int *>(dev_alloc(size_t(Mp) * sizeof(int), s));
-  int *eb = static_cast<int *>(dev_alloc(size_t(Np) * sizeof(int), s));
-  {
-    ProfScope prof("oz_pack", s, 0.0, 8.0 * (M * K + K * N) * 2 + 2.0 * S * (Mp + Np) * Kp);
-    // op(A)[m, k]: contiguous along k unless ta; op(B) as rows n: element (n, k) is
-    // B[k * ldb + n] (strided in k) unless tb
-    if (!ta) oz_rowexp_contig<<<unsigned((Mp * 32 + 255) / 256), 256, 0, s>>>(A, lda, M, K, ea, Mp);
-    else oz_rowexp_strided<<<unsigned((Mp + 255) / 256), 256, 0, s>>>(A, lda, M, K, ea, Mp);
-    if (tb) oz_rowexp_contig<<<unsigned((Np * 32 + 255) / 256), 256, 0, s>>>(B, ldb, N, K, eb, Np);
-    else oz_rowexp_strided<<<unsigned((Np + 255) / 256), 256, 0, s>>>(B, ldb, N, K, eb, Np);
-    oz_digits_kernel<S><<<dim3(unsigned(Kp / 32), unsigned(Mp / 32)), 256, 0, s>>>(A, lda, ta, M, K, Kp, ea, Pa);
-    oz_digits_kernel<S><<<dim3(unsigned(Kp / 32), unsigned(Np / 32)), 256, 0, s>>>(B, ldb, !tb, N, K, Kp, eb, Pb);
-    count_launch(4);
-    check_launch("oz_pack");
+}  // namespace
+
+// Packed operand: the digits of op(X) (rows x K) as rows_pad x S Kp BF16 and the
+// per-row maxima (bit patterns) that fix the row exponents.
+struct OzPacked {
+  int S = 0;
+  int64_t rows = 0, rows_pad = 0, K = 0, Kp = 0;
+  __nv_bfloat16 *P = nullptr;
+  unsigned long long *mx = nullptr;
+  cudaStream_t s = nullptr;
+  ~OzPacked() {
+    if (P) dev_free(P, s);
+    if (mx) dev_free(mx, s);
   }
-  const CUtensorMap ma = oz_map(Pa, Mp, S * Kp, OBM);
-  const CUtensorMap mb = oz_map(Pb, Np, S * Kp, BN);
+};
+
+namespace {
+
+template <int S>
+std::shared_ptr<OzPacked> oz_pack(const double *X, int64_t ld, bool trans, int64_t rows, int64_t K, int64_t align,
+                                  cudaStream_t s) {
+  auto out = std::make_shared<OzPacked>();
+  out->S = S;
+  out->rows = rows;
+  out->K = K;
+  out->Kp = (K + 63) / 64 * 64;  // whole 64-element pack tiles (two K slices)
+  out->rows_pad = (rows + align - 1) / align * align;
+  out->s = s;
+  IPEPS_REQUIRE(out->rows_pad / 32 <= 65535 && S * out->Kp <= 2147483647 && out->Kp / OBK <= (int64_t(1) << 24),
+                "oz_gemm: problem too large");
+  out->P = static_cast<__nv_bfloat16 *>(dev_alloc(size_t(out->rows_pad) * S * out->Kp * 2, s));
+  out->mx = static_cast<unsigned long long *>(dev_alloc(size_t(out->rows_pad) * 8, s));
+  ProfScope prof("oz_pack", s, 0.0, 8.0 * rows * K + 2.0 * S * out->rows_pad * out->Kp);
+  IPEPS_CUDA(cudaMemsetAsync(out->mx, 0, size_t(out->rows_pad) * 8, s));
+  const dim3 grid(unsigned(out->Kp / 64), unsigned(out->rows_pad / 32));
+  oz_absmax_kernel<<<grid, 256, 0, s>>>(X, ld, trans, rows, K, out->mx);
+  oz_digits_kernel<S><<<grid, 256, 0, s>>>(X, ld, trans, rows, K, out->Kp, out->mx, out->P);
+  count_launch(2);
+  check_launch("oz_pack");
+  return out;
+}
+
+template <int S, int BN>
+void oz_multiply(const OzPacked &a, const OzPacked &b, int64_t M, int64_t N, double alpha, double beta, double *C,
+                 int64_t ldc, cudaStream_t s) {
+  IPEPS_REQUIRE(a.S == S && b.S == S && a.Kp == b.Kp && a.rows_pad % OBM == 0 && b.rows_pad % BN == 0 &&
+                    a.rows == M && b.rows == N,
+                "oz_gemm: packed operands do not match");
+  const int64_t Kp = a.Kp, Mp = a.rows_pad, Np = b.rows_pad, K = a.K;
+  const CUtensorMap ma = oz_map(a.P, Mp, S * Kp, OBM);
+  const CUtensorMap mb = oz_map(b.P, Np, S * Kp, BN);
   // split K when the output tiles leave SMs idle; every split covers whole slices
   const int nk = int(Kp / OBK);
   const int64_t tiles = (Mp / OBM) * (Np / BN);
@@ -433,7 +498,8 @@ void oz_run(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, con
   if (Z > 1) W = static_cast<double *>(dev_alloc(size_t(Z) * M * N * sizeof(double), s));
   int *err = tc_error_word();
   {
-    ProfScope prof(shape_class("oz_gemm", M, N, K), s, 2.0 * M * N * K,
+    static const char *names[9] = {"", "", "oz2_gemm", "oz3_gemm", "", "", "", "", "oz8_gemm"};
+    ProfScope prof(shape_class(names[S], M, N, K), s, 2.0 * M * N * K,
                    2.0 * S * (Mp + Np) * Kp + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
     constexpr size_t smem = size_t(ostages<S, BN>()) * stage_bytes<S, BN>() + 1024;
     static bool attr = false;
@@ -443,11 +509,11 @@ void oz_run(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, con
     }
     dim3 grid(unsigned(Np / BN), unsigned(Mp / OBM), unsigned(Z));
     if (Z > 1)
-      oz_gemm_kernel<S, BN><<<grid, othreads<BN>(), smem, s>>>(ma, mb, ea, eb, M, N, int(Kp), nk, kper, alpha, 0.0,
-                                                              W, N, M * N, err);
+      oz_gemm_kernel<S, BN><<<grid, othreads<BN>(), smem, s>>>(ma, mb, a.mx, b.mx, M, N, int(Kp), nk, kper, alpha,
+                                                              0.0, W, N, M * N, err);
     else
-      oz_gemm_kernel<S, BN><<<grid, othreads<BN>(), smem, s>>>(ma, mb, ea, eb, M, N, int(Kp), nk, kper, alpha, beta,
-                                                              C, ldc, 0, err);
+      oz_gemm_kernel<S, BN><<<grid, othreads<BN>(), smem, s>>>(ma, mb, a.mx, b.mx, M, N, int(Kp), nk, kper, alpha,
+                                                              beta, C, ldc, 0, err);
     count_launch();
     check_launch("oz_gemm");
     if (Z > 1) {
@@ -457,26 +523,55 @@ void oz_run(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, con
     }
   }
   if (W) dev_free(W, s);
-  dev_free(Pa, s);
-  dev_free(Pb, s);
-  dev_free(ea, s);
-  dev_free(eb, s);
+}
+
+template <int S, int BN>
+void oz_run(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+            const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s,
+            const OzPacked *pa) {
+  std::shared_ptr<OzPacked> own;
+  if (!pa) {
+    own = oz_pack<S>(A, lda, ta, M, K, OBM, s);
+    pa = own.get();
+  }
+  // op(B) as rows n: element (n, k) is B[k * ldb + n] (strided in k) unless tb
+  auto pb = oz_pack<S>(B, ldb, !tb, N, K, BN, s);
+  oz_multiply<S, BN>(*pa, *pb, M, N, alpha, beta, C, ldc, s);
 }
 
 }  // namespace
 
 void gemm_oz(int slices, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,
-             int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s) {
+             int64_t lda, const double *B, int64_t ldb, double beta, double *C, int64_t ldc, cudaStream_t s,
+             const OzPacked *packed_a) {
   if (M <= 0 || N <= 0) return;
   if (K <= 0) {
     gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);  // C = beta C
     return;
   }
+  IPEPS_REQUIRE(!packed_a || packed_a->S == slices, "oz_gemm: packed operand has another digit count");
   switch (slices) {
-    case 2: oz_run<2, 128>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s); break;
-    case 3: oz_run<3, 128>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s); break;
-    case 8: oz_run<8, 64>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s); break;
+    case 2: oz_run<2, 128>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, packed_a); break;
+    case 3: oz_run<3, 128>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, packed_a); break;
+    case 8: oz_run<8, 64>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, packed_a); break;
     default: throw Error(IPEPS_ERR_ARG, "oz_gemm: slices must be 2, 3 or 8");
+  }
+}
+
+std::shared_ptr<OzPacked> pack_left_fp64(bool ta, int64_t M, int64_t K, const double *A, int64_t lda,
+                                         cudaStream_t s) {
+  if (fp64_policy() != Prec::FP64_TC || M <= 0 || K <= 0) return nullptr;
+  return oz_pack<8>(A, lda, ta, M, K, OBM, s);
+}
+
+void gemm_f64_packed(const OzPacked *pa, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
+                     const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                     int64_t ldc, cudaStream_t s) {
+  if (pa && K > 0 && M > 0 && N > 0 && oz_worthwhile(M, N, K)) {
+    IPEPS_REQUIRE(pa->rows == M && pa->K == K, "gemm_f64_packed: packed operand has another shape");
+    gemm_oz(8, ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, pa);
+  } else {
+    gemm_f64(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s);
   }
 }
 

@@ -183,9 +183,15 @@ bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, dou
                   double *V, cudaStream_t s, int *iters, bool tc) {
   // tc: the two N x N by N x k products on the 3xTF32 tensor-core path (all-TF32
   // throughput mode); their error floor is then ~1e-6 of |M|, not FP64 rounding
+  // M and M^T are multiplied once per iteration each: pack their digits once
+  std::shared_ptr<OzPacked> pm, pmt;
+  if (!tc) {
+    pm = pack_left_fp64(false, N, N, M, N, s);
+    pmt = pack_left_fp64(true, N, N, M, N, s);
+  }
   auto big = [&](bool ta, const double *B, double *C) {
     if (tc) gemm_tf32x3(ta, false, N, k, N, 1.0, M, N, B, k, 0.0, C, k, s);
-    else gemm_f64(ta, false, N, k, N, 1.0, M, N, B, k, 0.0, C, k, s);
+    else gemm_f64_packed(ta ? pmt.get() : pm.get(), ta, false, N, k, N, 1.0, M, N, B, k, 0.0, C, k, s);
   };
   const double stall = tc ? 1e-2 : 1e-6;
   IPEPS_REQUIRE(k >= chi && k <= N && k % 2 == 0, "svd_subspace: bad block size");
@@ -405,7 +411,10 @@ struct TruncSVDNode : Node {
     } else {
       scale_cols(2 * n, c, R.p, invs.p, X.p, s);
     }
-    // K (X, Y) = (X S - Mperp Y, Y S - Mperp^T X)
+    // K (X, Y) = (X S - Mperp Y, Y S - Mperp^T X); M and M^T enter every
+    // application: their digits are packed once for the whole solve
+    auto pm = pack_left_fp64(false, n, n, Mp, n, s);
+    auto pmt = pack_left_fp64(true, n, n, Mp, n, s);
     auto K = [&](const double *inX, double *out) {
       const double *iU = inX, *iV = inX + n * c;
       double *oU = out, *oV = out + n * c;
@@ -413,14 +422,14 @@ struct TruncSVDNode : Node {
       IPEPS_CUDA(cudaMemcpyAsync(tmp.p, iV, n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
       gemm_f64(true, false, c, c, n, 1.0, Vk.p, kb, iV, c, 0.0, sm.p, c, s);
       gemm_f64(false, false, n, c, c, -1.0, Vk.p, kb, sm.p, c, 1.0, tmp.p, c, s);
-      gemm_f64(false, false, n, c, n, 1.0, Mp, n, tmp.p, c, 0.0, oU, c, s);
+      gemm_f64_packed(pm.get(), false, false, n, c, n, 1.0, Mp, n, tmp.p, c, 0.0, oU, c, s);
       gemm_f64(true, false, c, c, n, 1.0, Uk.p, kb, oU, c, 0.0, sm.p, c, s);
       gemm_f64(false, false, n, c, c, -1.0, Uk.p, kb, sm.p, c, 1.0, oU, c, s);
       // Mperp^T X: P_V M^T P_U X
       IPEPS_CUDA(cudaMemcpyAsync(tmp.p, iU, n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
       gemm_f64(true, false, c, c, n, 1.0, Uk.p, kb, iU, c, 0.0, sm.p, c, s);
       gemm_f64(false, false, n, c, c, -1.0, Uk.p, kb, sm.p, c, 1.0, tmp.p, c, s);
-      gemm_f64(true, false, n, c, n, 1.0, Mp, n, tmp.p, c, 0.0, oV, c, s);
+      gemm_f64_packed(pmt.get(), true, false, n, c, n, 1.0, Mp, n, tmp.p, c, 0.0, oV, c, s);
       gemm_f64(true, false, c, c, n, 1.0, Vk.p, kb, oV, c, 0.0, sm.p, c, s);
       gemm_f64(false, false, n, c, c, -1.0, Vk.p, kb, sm.p, c, 1.0, oV, c, s);
       // out = in S - out

@@ -27,11 +27,17 @@ def ip():
     return ipeps
 
 
+@pytest.mark.parametrize("prec", ["FP64", "FP64_TC"])
 @pytest.mark.parametrize("name", ["random_d4", "neel_seed_d4"])
-def test_truncated_path_fp64(ip, name):
+def test_truncated_path_fp64(ip, name, prec):
+    # FP64_TC: every large GEMM from BF16 digits on the tensor cores, same FP64 bar
     cell = inputs.uniform_cell(1, 1, 2, 4, 3) if name == "random_d4" else inputs.WORKLOADS["heis_d4_chi64"]["gen"]()
     A = torch.as_tensor(ip.cell_tensor(cell), device="cuda")
-    env, it, err = ip.ctmrg(A, CHI, tol=1e-11, maxit=300)
+    ip.profile(True)
+    env, it, err = ip.ctmrg(A, CHI, tol=1e-11, maxit=300, prec=getattr(ip, prec))
+    if prec == "FP64_TC":
+        assert ip.profile_stats().get("oz8_gemm", {}).get("count", 0) > 0  # the tensor-core path ran
+    ip.profile(False)
     E, g = ip.energy_grad(A, env, ip.ham_heisenberg(True))
     Eo, go, info = OG.energy_and_gradient(cell, OM.heisenberg(True), CHI, tol=1e-11, return_info=True)
     assert abs(E - Eo) <= 1e-10
