@@ -76,10 +76,14 @@ typedef enum {
                            fixed point (error bound of an FP64 GEMM taken relative
                            to the row and column maxima); small GEMMs, SVD
                            rotations, reductions and GMRES stay FP64 */
-  IPEPS_BF16X3 = 4      /* BF16x3 contractions: the bulk GEMMs from 2 digits per
-                           operand (3 BF16 products per term, about 2^-15 of the
-                           row and column maxima), the four-corner and projector
-                           products and every other GEMM as IPEPS_FP64_TC */
+  IPEPS_BF16X3 = 4      /* BF16x3 contractions: enlarged corners, half systems and
+                           absorption from 2 digits per operand (3 BF16 products
+                           per term, about 2^-15 of the row and column maxima);
+                           the four-corner and projector products and every other
+                           GEMM as IPEPS_FP64_TC.  CTMRG runs BF16x3 iterations
+                           until the spectra change < 1e-6 (or stops improving),
+                           then IPEPS_FP64_TC iterations to tol; the gradient is
+                           that of the IPEPS_FP64_TC fixed point. */
 } ipeps_prec;
 
 typedef struct {

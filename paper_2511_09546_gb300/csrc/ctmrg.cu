@@ -395,6 +395,8 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
     if (change < 0.7 * best) { best = change; since_best = 0; }
     else ++since_best;
     if (phase == Prec::TF32X3 && (change < kSplitSwitch || since_best >= 10)) phase = Prec::FP64;
+    // BF16x3 iterations likewise hand over to FP64-grade tensor-core iterations
+    if (phase == Prec::BF16X3 && (change < kSplitSwitch || since_best >= 10)) phase = Prec::FP64_TC;
     if (phase == Prec::TF32X3_ALL && since_best >= 10) break;  // at the noise floor
   }
   e.prec = phase;
