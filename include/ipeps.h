@@ -215,6 +215,86 @@ ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham h
                             const ipeps_opts *opts, ipeps_iter_cb cb, void *user,
                             ipeps_stream_t stream);
 
+/* ------------------------------------------------------------ serving */
+/* Many independent optimisations on one GPU (no counterpart in the paper,
+ * which runs one optimisation at a time, Sec. IV).  A server owns `slots`
+ * worker threads; each takes the admitted job whose last L-BFGS iteration is
+ * oldest and runs its next iteration (ipeps_optimize's iteration) on the job's
+ * own CUDA stream, so iterations of different jobs overlap on the device and
+ * jobs that arrive while others run start as soon as a slot and memory are
+ * free.  Each job's tensors, environment, L-BFGS history and tapes stay on the
+ * device from admission to its end.  Admission by device memory: a queued job
+ * is admitted (oldest first) when the sum of ipeps_job_footprint over admitted
+ * jobs stays within hbm_budget_bytes (a job larger than the budget runs alone).
+ * With autotune != 0 the first job of every (d, D, chi, cell, precision) class
+ * times one CTMRG iteration at three settings of the tensor-core crossover
+ * (the GEMM size above which the BF16-digit kernel is used) and the class
+ * keeps the fastest.  A job's result is independent of the other jobs: every
+ * kernel is deterministic and each job has private buffers.  The device is
+ * the one current at ipeps_server_create.  All calls are thread safe;
+ * messages of failed calls come from ipeps_server_last_error(). */
+typedef struct {
+  int slots;               /* worker threads (1 .. 64), default 3 */
+  size_t hbm_budget_bytes; /* 0: 80% of the free device memory at creation */
+  int autotune;            /* per-class tensor-core crossover, default 1 */
+} ipeps_server_opts;
+
+typedef struct ipeps_server_s *ipeps_server;
+
+typedef struct {
+  ipeps_shape shape;    /* unit cell */
+  const double *A_host; /* starting tensors, host, layout above (copied) */
+  ipeps_ham ham;        /* Hamiltonian (copied; may be destroyed after submit) */
+  ipeps_opts opts;      /* as for ipeps_optimize */
+} ipeps_job_desc;
+
+typedef enum {
+  IPEPS_JOB_QUEUED = 0,
+  IPEPS_JOB_RUNNING = 1,
+  IPEPS_JOB_DONE = 2,      /* maxiter, gtol or E_target reached */
+  IPEPS_JOB_FAILED = 3,    /* see ipeps_job_result.error */
+  IPEPS_JOB_CANCELLED = 4
+} ipeps_job_state;
+
+typedef struct {
+  int state;              /* ipeps_job_state */
+  int iterations;         /* L-BFGS iterations completed */
+  double E, gnorm;        /* energy per site and |g| of the current point */
+  double queued_ms;       /* submit to admission */
+  double run_ms;          /* admission to end (so far, while running) */
+  double iter_ms_p50, iter_ms_p99; /* wall time per iteration of this job */
+  size_t footprint_bytes; /* admission estimate */
+  int error;              /* ipeps_status of a failed job */
+} ipeps_job_result;
+
+typedef struct {
+  int jobs_done, jobs_running, jobs_queued;
+  int64_t iterations;            /* iterations of ended jobs */
+  double iter_ms_p50, iter_ms_p99;
+  size_t hbm_in_use_bytes, hbm_budget_bytes;
+} ipeps_server_stats;
+
+void ipeps_server_opts_default(ipeps_server_opts *opts);
+/* Estimated device bytes of one job (environment, recorded tapes with their
+ * cotangents, line-search copies); 0 for an invalid shape. */
+size_t ipeps_job_footprint(const ipeps_shape *shape, int chi);
+ipeps_status ipeps_server_create(const ipeps_server_opts *opts, ipeps_server *out);
+/* Queue a job; *job_id identifies it.  Errors: IPEPS_ERR_ARG (shape, options,
+ * non-finite A, Hamiltonian of another d). */
+ipeps_status ipeps_server_submit(ipeps_server srv, const ipeps_job_desc *desc, uint64_t *job_id);
+/* Non-blocking snapshot of a job. */
+ipeps_status ipeps_server_poll(ipeps_server srv, uint64_t job_id, ipeps_job_result *res);
+/* Block until the job has ended; IPEPS_ERR_TIMEOUT after timeout_s seconds. */
+ipeps_status ipeps_server_wait(ipeps_server srv, uint64_t job_id, double timeout_s);
+/* Stop a job: a queued job at once, a running one after its current iteration. */
+ipeps_status ipeps_server_cancel(ipeps_server srv, uint64_t job_id);
+/* Final tensors of an ended job (host, n >= Lx Ly d D^4 doubles). */
+ipeps_status ipeps_server_tensor(ipeps_server srv, uint64_t job_id, double *A_host, size_t n);
+ipeps_status ipeps_server_get_stats(ipeps_server srv, ipeps_server_stats *stats);
+const char *ipeps_server_last_error(void);
+/* Waits for the iterations in flight, frees every job and joins the workers. */
+void ipeps_server_destroy(ipeps_server srv);
+
 /* ------------------------------------------------------------- GEMM */
 /* The contraction engine's GEMM (row-major): C = alpha op(A) op(B) + beta C,
  * op(A) M x K (ta != 0: A stored K x M), op(B) K x N (tb != 0: B stored

@@ -15,12 +15,6 @@
 #include "profile.h"
 #include "engine.h"
 
-struct ipeps_env_s {
-  ipeps::EnvImpl impl;
-};
-struct ipeps_ham_s {
-  ipeps::HamImpl impl;
-};
 
 namespace ipeps {
 

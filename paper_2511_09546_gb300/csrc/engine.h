@@ -37,8 +37,11 @@ struct PolicyScope {
 };
 // FP64-grade products for contractions run in precision p
 inline Prec fp64_grade_of(Prec p) { return (p == Prec::FP64_TC || p == Prec::BF16X3) ? Prec::FP64_TC : Prec::FP64; }
-// the shape is large enough for the slice GEMM to beat the DFMA kernels
+// the shape is large enough for the slice GEMM to beat the DFMA kernels:
+// M N K at least oz_threshold() (this thread's crossover, 2^23 by default;
+// the server's autotuner sets it per problem shape)
 bool oz_worthwhile(int64_t m, int64_t n, int64_t k);
+double &oz_threshold();
 // C = alpha op(A) op(B) + beta C on the BF16 tensor cores with `slices` 7-bit
 // digits per operand (2: BF16x3, 3, or 8: FP64-grade); row-major, FP64 in and out
 struct OzPacked;

@@ -164,8 +164,13 @@ Prec &fp64_policy() {
 
 // The slice GEMM packs both operands (4 launches) and pads M to 128, N to 64
 // and K to 64; below about 2^23 multiply-adds the DFMA kernels finish first.
+double &oz_threshold() {
+  static thread_local double t = double(1 << 23);
+  return t;
+}
+
 bool oz_worthwhile(int64_t m, int64_t n, int64_t k) {
-  return m >= 16 && n >= 8 && k >= 16 && double(m) * n * k >= double(1 << 23);
+  return m >= 16 && n >= 8 && k >= 16 && double(m) * n * k >= oz_threshold();
 }
 
 void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double *A,

@@ -123,9 +123,38 @@ using MatVec = std::function<void(const double *x, double *y)>;
 double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int krylov, int restarts,
                  double rtol, cudaStream_t s, int *matvecs);
 
+// ---- optimiser (optimize.cu)
+class LbfgsRun {
+ public:
+  LbfgsRun(const Cell &c, const HamImpl &H, const ipeps_opts &o, cudaStream_t s);
+  ~LbfgsRun();
+  LbfgsRun(const LbfgsRun &) = delete;
+  LbfgsRun &operator=(const LbfgsRun &) = delete;
+  ipeps_iter_info start(const double *A_dev);  // evaluates the starting point (copied)
+  bool step(ipeps_iter_info *info);            // one iteration; false when the run has ended
+  bool finished() const;
+  int iteration() const;
+  double energy() const;
+  void copy_tensor(double *A_dev) const;       // current tensors (stream-ordered)
+
+ private:
+  struct Impl;
+  std::unique_ptr<Impl> impl_;
+};
+ipeps_status optimize_impl(const Cell &c, double *A_dev, const HamImpl &H, const ipeps_opts &o,
+                           ipeps_iter_cb cb, void *user, cudaStream_t s);
+
 // ---- gradient (adjoint.cu)
 double energy_only(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl &H, cudaStream_t s);
 double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl &H, double *grad,
                    cudaStream_t s, double *adj_resid, int *adj_mv, double *fp_resid);
 
 }  // namespace ipeps
+
+// the opaque handles of the C ABI
+struct ipeps_env_s {
+  ipeps::EnvImpl impl;
+};
+struct ipeps_ham_s {
+  ipeps::HamImpl impl;
+};

@@ -116,202 +116,272 @@ struct Driver {
 
 }  // namespace
 
-ipeps_status optimize_impl(const Cell &c, double *A_dev, const HamImpl &H, const ipeps_opts &o,
-                           ipeps_iter_cb cb, void *user, cudaStream_t s) {
-  Driver drv{c, H, o, s, int64_t(c.nsites()) * c.tsize()};
-  const int64_t n = drv.n;
-  auto t0 = std::chrono::steady_clock::now();
-  auto cur = std::make_unique<Point>();
-  cur->x = DBuf(size_t(n), s);
-  IPEPS_CUDA(cudaMemcpyAsync(cur->x.p, A_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  {
-    EnvImpl e0;
-    e0.cell = c;
-    e0.chi = o.chi;
-    e0.s = s;
-    e0.buf = DBuf(size_t(e0.total()), s);
-    env_init(e0, cur->x.p, s);
-    drv.evaluate(*cur, e0);
-  }
-  if (!cur->ok) throw Error(IPEPS_ERR_NOT_CONVERGED, "optimize: starting point did not converge");
+// One optimisation as a resumable state machine: start() evaluates the
+// starting point, every step() runs one L-BFGS iteration (two-loop direction,
+// Hager-Zhang line search, history update).  optimize_impl drives one run to
+// its end; the server interleaves the steps of many runs.
+struct LbfgsRun::Impl {
+  Driver drv;
+  int64_t n;
+  std::unique_ptr<Point> cur;
   struct Pair { DBuf s, y; double rho; };
   std::deque<Pair> hist;
   double f_prev = NAN;
-  auto report = [&](int k, double alpha, double delta, int evals) {
-    ipeps_iter_info info{};
-    info.iter = k;
-    info.E = cur->f;
-    info.gnorm = std::sqrt(ddot(n, cur->g.p, cur->g.p, s));
-    info.alpha = alpha;
-    info.delta = delta;
-    info.evals = evals;
-    info.ctm_iters = cur->ctm_iters;
+  int k = 0;
+  bool done = false;
+  DBuf d, q, r, tmp;
+  std::chrono::steady_clock::time_point t0;
+  Impl(const Cell &c, const HamImpl &H, const ipeps_opts &o, cudaStream_t s)
+      : drv{c, H, o, s, int64_t(c.nsites()) * c.tsize()}, n(int64_t(c.nsites()) * c.tsize()) {}
+
+  ipeps_iter_info info(int it, double alpha, double delta, int evals) {
+    ipeps_iter_info inf{};
+    inf.iter = it;
+    inf.E = cur->f;
+    inf.gnorm = std::sqrt(ddot(n, cur->g.p, cur->g.p, drv.s));
+    inf.alpha = alpha;
+    inf.delta = delta;
+    inf.evals = evals;
+    inf.ctm_iters = cur->ctm_iters;
     auto t1 = std::chrono::steady_clock::now();
-    info.wall_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    inf.wall_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     t0 = t1;
-    if (cb && cb(&info, user)) return true;
+    return inf;
+  }
+};
+
+LbfgsRun::LbfgsRun(const Cell &c, const HamImpl &H, const ipeps_opts &o, cudaStream_t s)
+    : impl_(new Impl(c, H, o, s)) {}
+LbfgsRun::~LbfgsRun() = default;
+
+ipeps_iter_info LbfgsRun::start(const double *A_dev) {
+  Impl &m = *impl_;
+  Driver &drv = m.drv;
+  const cudaStream_t s = drv.s;
+  const int64_t n = m.n;
+  m.t0 = std::chrono::steady_clock::now();
+  m.cur = std::make_unique<Point>();
+  m.cur->x = DBuf(size_t(n), s);
+  IPEPS_CUDA(cudaMemcpyAsync(m.cur->x.p, A_dev, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  {
+    EnvImpl e0;
+    e0.cell = drv.c;
+    e0.chi = drv.o.chi;
+    e0.s = s;
+    e0.buf = DBuf(size_t(e0.total()), s);
+    env_init(e0, m.cur->x.p, s);
+    drv.evaluate(*m.cur, e0);
+  }
+  if (!m.cur->ok) throw Error(IPEPS_ERR_NOT_CONVERGED, "optimize: starting point did not converge");
+  m.d = DBuf(size_t(n), s);
+  m.q = DBuf(size_t(n), s);
+  m.r = DBuf(size_t(n), s);
+  m.tmp = DBuf(size_t(n), s);
+  return m.info(0, 0.0, 0.0, 1);
+}
+
+bool LbfgsRun::finished() const { return impl_->done; }
+int LbfgsRun::iteration() const { return impl_->k; }
+double LbfgsRun::energy() const { return impl_->cur ? impl_->cur->f : NAN; }
+
+void LbfgsRun::copy_tensor(double *A_dev) const {
+  const Impl &m = *impl_;
+  if (!m.cur || !m.cur->x.p) return;
+  IPEPS_CUDA(cudaMemcpyAsync(A_dev, m.cur->x.p, m.n * sizeof(double), cudaMemcpyDeviceToDevice, m.drv.s));
+}
+
+bool LbfgsRun::step(ipeps_iter_info *out) {
+  Impl &m = *impl_;
+  if (m.done) return false;
+  Driver &drv = m.drv;
+  const ipeps_opts &o = drv.o;
+  const cudaStream_t s = drv.s;
+  const int64_t n = m.n;
+  auto &cur = m.cur;
+  auto &hist = m.hist;
+  DBuf &d = m.d, &q = m.q, &r = m.r, &tmp = m.tmp;
+  if (m.k >= o.maxiter) {
+    m.done = true;
     return false;
+  }
+  const double gg = ddot(n, cur->g.p, cur->g.p, s);
+  if (std::sqrt(gg) < o.gtol || cur->f <= o.E_target) {
+    m.done = true;
+    return false;
+  }
+  const double f_prev = m.f_prev;
+  double delta = (o.delta_rule == 0 || std::isnan(f_prev)) ? std::max(gg, 1e-12)
+                                                           : std::max(std::fabs(cur->f - f_prev), 1e-12);
+  // ---- two-loop recursion
+  IPEPS_CUDA(cudaMemcpyAsync(q.p, cur->g.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  std::vector<double> alphas;
+  for (auto it = hist.rbegin(); it != hist.rend(); ++it) {
+    double a = it->rho * ddot(n, it->s.p, q.p, s);
+    axpy(n, -a, it->y.p, q.p, s);
+    alphas.push_back(a);
+  }
+  double gamma = 1.0;
+  if (o.precondition) {
+    drv.precond(*cur, q.p, delta, r.p);
+    if (!hist.empty()) {
+      drv.precond(*cur, hist.back().y.p, delta, tmp.p);
+      gamma = ddot(n, hist.back().s.p, hist.back().y.p, s) / ddot(n, hist.back().y.p, tmp.p, s);
+    }
+  } else {
+    IPEPS_CUDA(cudaMemcpyAsync(r.p, q.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (!hist.empty())
+      gamma = ddot(n, hist.back().s.p, hist.back().y.p, s) / ddot(n, hist.back().y.p, hist.back().y.p, s);
+  }
+  scal(n, gamma, r.p, s);
+  {
+    size_t i = 0;
+    for (auto it = hist.begin(); it != hist.end(); ++it, ++i) {
+      double a = alphas[alphas.size() - 1 - i];
+      double b = it->rho * ddot(n, it->y.p, r.p, s);
+      axpy(n, a - b, it->s.p, r.p, s);
+    }
+  }
+  axpby(n, -1.0, r.p, 0.0, d.p, s);
+  double dg = ddot(n, d.p, cur->g.p, s);
+  if (!(dg < 0.0)) {  // not a descent direction: restart
+    hist.clear();
+    if (o.precondition) drv.precond(*cur, cur->g.p, delta, r.p);
+    else IPEPS_CUDA(cudaMemcpyAsync(r.p, cur->g.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    axpby(n, -1.0, r.p, 0.0, d.p, s);
+    dg = ddot(n, d.p, cur->g.p, s);
+  }
+  double c0 = (!hist.empty() || o.precondition) ? 1.0 : 0.01 * absmax(n, cur->x.p, s) / absmax(n, d.p, s);
+  // ---- Hager-Zhang line search
+  const double phi0 = cur->f, dphi0 = dg;
+  const double hz_delta = 0.1, hz_sigma = 0.9, hz_eps = 1e-6, hz_theta = 0.5, hz_gamma = 0.66,
+               hz_rho = 5.0;
+  const int max_evals = 40;
+  const double fmax = phi0 + hz_eps * std::fabs(phi0);
+  std::map<double, std::unique_ptr<Point>> cache;
+  std::map<double, std::pair<double, double>> vals;  // a -> (phi, dphi)
+  vals[0.0] = {phi0, dphi0};
+  double found = -1.0;
+  struct Stop {};
+  auto ev = [&](double a) -> std::pair<double, double> {
+    auto it = vals.find(a);
+    if (it != vals.end()) return it->second;
+    if (int(vals.size()) > max_evals) throw Stop{};
+    auto p = std::make_unique<Point>();
+    p->x = DBuf(size_t(n), s);
+    IPEPS_CUDA(cudaMemcpyAsync(p->x.p, cur->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    axpy(n, a, d.p, p->x.p, s);
+    drv.evaluate(*p, cur->env);
+    std::pair<double, double> v{INFINITY, INFINITY};
+    if (p->ok) v = {p->f, ddot(n, p->g.p, d.p, s)};
+    vals[a] = v;
+    cache[a] = std::move(p);
+    bool t1 = (v.first - phi0 <= hz_delta * a * dphi0) && (v.second >= hz_sigma * dphi0);
+    bool t2 = ((2.0 * hz_delta - 1.0) * dphi0 >= v.second) && (v.second >= hz_sigma * dphi0) &&
+              (v.first <= fmax);
+    if (std::isfinite(v.first) && (t1 || t2)) {
+      found = a;
+      throw Stop{};
+    }
+    return v;
   };
-  if (report(0, 0.0, 0.0, 1)) {
-    IPEPS_CUDA(cudaMemcpyAsync(A_dev, cur->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  auto bisect = [&](double a, double b) -> std::pair<double, double> {
+    for (;;) {
+      double dd = (1.0 - hz_theta) * a + hz_theta * b;
+      auto v = ev(dd);
+      if (v.second >= 0) return {a, dd};
+      if (v.first <= fmax) a = dd;
+      else b = dd;
+    }
+  };
+  auto update = [&](double a, double b, double cc) -> std::pair<double, double> {
+    if (!(a < cc && cc < b)) return {a, b};
+    auto v = ev(cc);
+    if (v.second >= 0) return {a, cc};
+    if (v.first <= fmax) return {cc, b};
+    return bisect(a, cc);
+  };
+  auto secant = [&](double a, double b) {
+    double da = vals[a].second, db = vals[b].second;
+    if (db == da || !std::isfinite(da) || !std::isfinite(db)) return 0.5 * (a + b);
+    return (a * db - b * da) / (db - da);
+  };
+  try {
+    // bracket
+    double a = 0.0, b = 0.0, cc = c0, good = 0.0;
+    for (;;) {
+      auto v = ev(cc);
+      if (v.second >= 0) { a = good; b = cc; break; }
+      if (v.first > fmax) { auto ab = bisect(0.0, cc); a = ab.first; b = ab.second; break; }
+      good = cc;
+      cc *= hz_rho;
+    }
+    for (;;) {
+      double cs = secant(a, b);
+      auto AB = update(a, b, cs);
+      if (cs == AB.second) AB = update(AB.first, AB.second, secant(b, AB.second));
+      else if (cs == AB.first) AB = update(AB.first, AB.second, secant(a, AB.first));
+      if (AB.second - AB.first > hz_gamma * (b - a))
+        AB = update(AB.first, AB.second, 0.5 * (AB.first + AB.second));
+      a = AB.first;
+      b = AB.second;
+    }
+  } catch (Stop &) {
+  }
+  int nev = int(vals.size()) - 1;
+  if (found < 0.0) {  // budget spent: best finite point, if any
+    double bestf = INFINITY;
+    for (auto &kv : vals)
+      if (kv.first > 0.0 && kv.second.first < bestf) { bestf = kv.second.first; found = kv.first; }
+    if (!(bestf < phi0)) {
+      m.done = true;
+      throw Error(IPEPS_ERR_NOT_CONVERGED, "optimize: line search found no decrease");
+    }
+  }
+  std::unique_ptr<Point> nxt = std::move(cache[found]);
+  cache.clear();
+  // ---- history update
+  Impl::Pair pr{DBuf(size_t(n), s), DBuf(size_t(n), s), 0.0};
+  axpby(n, found, d.p, 0.0, pr.s.p, s);
+  IPEPS_CUDA(cudaMemcpyAsync(pr.y.p, nxt->g.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  axpy(n, -1.0, cur->g.p, pr.y.p, s);
+  double sy = ddot(n, pr.s.p, pr.y.p, s);
+  double ns = std::sqrt(ddot(n, pr.s.p, pr.s.p, s)), ny = std::sqrt(ddot(n, pr.y.p, pr.y.p, s));
+  if (sy > 1e-16 * ns * ny) {
+    pr.rho = 1.0 / sy;
+    hist.push_back(std::move(pr));
+    while (int(hist.size()) > o.history) hist.pop_front();
+  }
+  m.f_prev = cur->f;
+  cur = std::move(nxt);
+  ++m.k;
+  if (out) *out = m.info(m.k, found, delta, nev);
+  return true;
+}
+
+ipeps_status optimize_impl(const Cell &c, double *A_dev, const HamImpl &H, const ipeps_opts &o,
+                           ipeps_iter_cb cb, void *user, cudaStream_t s) {
+  LbfgsRun run(c, H, o, s);
+  ipeps_iter_info info = run.start(A_dev);
+  auto finish = [&]() {
+    run.copy_tensor(A_dev);
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+  };
+  if (cb && cb(&info, user)) {
+    finish();
     return IPEPS_ERR_CANCELLED;
   }
-  DBuf d(size_t(n), s), q(size_t(n), s), r(size_t(n), s), tmp(size_t(n), s);
-  for (int k = 0; k < o.maxiter; ++k) {
-    const double gg = ddot(n, cur->g.p, cur->g.p, s);
-    if (std::sqrt(gg) < o.gtol || cur->f <= o.E_target) break;
-    double delta = (o.delta_rule == 0 || std::isnan(f_prev)) ? std::max(gg, 1e-12)
-                                                             : std::max(std::fabs(cur->f - f_prev), 1e-12);
-    // ---- two-loop recursion
-    IPEPS_CUDA(cudaMemcpyAsync(q.p, cur->g.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    std::vector<double> alphas;
-    for (auto it = hist.rbegin(); it != hist.rend(); ++it) {
-      double a = it->rho * ddot(n, it->s.p, q.p, s);
-      axpy(n, -a, it->y.p, q.p, s);
-      alphas.push_back(a);
-    }
-    double gamma = 1.0;
-    if (o.precondition) {
-      drv.precond(*cur, q.p, delta, r.p);
-      if (!hist.empty()) {
-        drv.precond(*cur, hist.back().y.p, delta, tmp.p);
-        gamma = ddot(n, hist.back().s.p, hist.back().y.p, s) / ddot(n, hist.back().y.p, tmp.p, s);
-      }
-    } else {
-      IPEPS_CUDA(cudaMemcpyAsync(r.p, q.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      if (!hist.empty())
-        gamma = ddot(n, hist.back().s.p, hist.back().y.p, s) / ddot(n, hist.back().y.p, hist.back().y.p, s);
-    }
-    scal(n, gamma, r.p, s);
-    {
-      size_t i = 0;
-      for (auto it = hist.begin(); it != hist.end(); ++it, ++i) {
-        double a = alphas[alphas.size() - 1 - i];
-        double b = it->rho * ddot(n, it->y.p, r.p, s);
-        axpy(n, a - b, it->s.p, r.p, s);
+  try {
+    while (run.step(&info)) {
+      if (cb && cb(&info, user)) {
+        finish();
+        return IPEPS_ERR_CANCELLED;
       }
     }
-    axpby(n, -1.0, r.p, 0.0, d.p, s);
-    double dg = ddot(n, d.p, cur->g.p, s);
-    if (!(dg < 0.0)) {  // not a descent direction: restart
-      hist.clear();
-      if (o.precondition) drv.precond(*cur, cur->g.p, delta, r.p);
-      else IPEPS_CUDA(cudaMemcpyAsync(r.p, cur->g.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      axpby(n, -1.0, r.p, 0.0, d.p, s);
-      dg = ddot(n, d.p, cur->g.p, s);
-    }
-    double c0 = (!hist.empty() || o.precondition) ? 1.0 : 0.01 * absmax(n, cur->x.p, s) / absmax(n, d.p, s);
-
-    // ---- Hager-Zhang line search
-    const double phi0 = cur->f, dphi0 = dg;
-    const double hz_delta = 0.1, hz_sigma = 0.9, hz_eps = 1e-6, hz_theta = 0.5, hz_gamma = 0.66,
-                 hz_rho = 5.0;
-    const int max_evals = 40;
-    const double fmax = phi0 + hz_eps * std::fabs(phi0);
-    std::map<double, std::unique_ptr<Point>> cache;
-    std::map<double, std::pair<double, double>> vals;  // a -> (phi, dphi)
-    vals[0.0] = {phi0, dphi0};
-    double found = -1.0;
-    struct Stop {};
-    auto ev = [&](double a) -> std::pair<double, double> {
-      auto it = vals.find(a);
-      if (it != vals.end()) return it->second;
-      if (int(vals.size()) > max_evals) throw Stop{};
-      auto p = std::make_unique<Point>();
-      p->x = DBuf(size_t(n), s);
-      IPEPS_CUDA(cudaMemcpyAsync(p->x.p, cur->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      axpy(n, a, d.p, p->x.p, s);
-      drv.evaluate(*p, cur->env);
-      std::pair<double, double> v{INFINITY, INFINITY};
-      if (p->ok) v = {p->f, ddot(n, p->g.p, d.p, s)};
-      vals[a] = v;
-      cache[a] = std::move(p);
-      bool t1 = (v.first - phi0 <= hz_delta * a * dphi0) && (v.second >= hz_sigma * dphi0);
-      bool t2 = ((2.0 * hz_delta - 1.0) * dphi0 >= v.second) && (v.second >= hz_sigma * dphi0) &&
-                (v.first <= fmax);
-      if (std::isfinite(v.first) && (t1 || t2)) {
-        found = a;
-        throw Stop{};
-      }
-      return v;
-    };
-    auto bisect = [&](double a, double b) -> std::pair<double, double> {
-      for (;;) {
-        double dd = (1.0 - hz_theta) * a + hz_theta * b;
-        auto v = ev(dd);
-        if (v.second >= 0) return {a, dd};
-        if (v.first <= fmax) a = dd;
-        else b = dd;
-      }
-    };
-    auto update = [&](double a, double b, double cc) -> std::pair<double, double> {
-      if (!(a < cc && cc < b)) return {a, b};
-      auto v = ev(cc);
-      if (v.second >= 0) return {a, cc};
-      if (v.first <= fmax) return {cc, b};
-      return bisect(a, cc);
-    };
-    auto secant = [&](double a, double b) {
-      double da = vals[a].second, db = vals[b].second;
-      if (db == da || !std::isfinite(da) || !std::isfinite(db)) return 0.5 * (a + b);
-      return (a * db - b * da) / (db - da);
-    };
-    try {
-      // bracket
-      double a = 0.0, b = 0.0, cc = c0, good = 0.0;
-      for (;;) {
-        auto v = ev(cc);
-        if (v.second >= 0) { a = good; b = cc; break; }
-        if (v.first > fmax) { auto ab = bisect(0.0, cc); a = ab.first; b = ab.second; break; }
-        good = cc;
-        cc *= hz_rho;
-      }
-      for (;;) {
-        double cs = secant(a, b);
-        auto AB = update(a, b, cs);
-        if (cs == AB.second) AB = update(AB.first, AB.second, secant(b, AB.second));
-        else if (cs == AB.first) AB = update(AB.first, AB.second, secant(a, AB.first));
-        if (AB.second - AB.first > hz_gamma * (b - a))
-          AB = update(AB.first, AB.second, 0.5 * (AB.first + AB.second));
-        a = AB.first;
-        b = AB.second;
-      }
-    } catch (Stop &) {
-    }
-    int nev = int(vals.size()) - 1;
-    if (found < 0.0) {  // budget spent: best finite point, if any
-      double bestf = INFINITY;
-      for (auto &kv : vals)
-        if (kv.first > 0.0 && kv.second.first < bestf) { bestf = kv.second.first; found = kv.first; }
-      if (!(bestf < phi0)) {
-        IPEPS_CUDA(cudaMemcpyAsync(A_dev, cur->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-        throw Error(IPEPS_ERR_NOT_CONVERGED, "optimize: line search found no decrease");
-      }
-    }
-    std::unique_ptr<Point> nxt = std::move(cache[found]);
-    cache.clear();
-    // ---- history update
-    Pair pr{DBuf(size_t(n), s), DBuf(size_t(n), s), 0.0};
-    axpby(n, found, d.p, 0.0, pr.s.p, s);
-    IPEPS_CUDA(cudaMemcpyAsync(pr.y.p, nxt->g.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    axpy(n, -1.0, cur->g.p, pr.y.p, s);
-    double sy = ddot(n, pr.s.p, pr.y.p, s);
-    double ns = std::sqrt(ddot(n, pr.s.p, pr.s.p, s)), ny = std::sqrt(ddot(n, pr.y.p, pr.y.p, s));
-    if (sy > 1e-16 * ns * ny) {
-      pr.rho = 1.0 / sy;
-      hist.push_back(std::move(pr));
-      while (int(hist.size()) > o.history) hist.pop_front();
-    }
-    f_prev = cur->f;
-    cur = std::move(nxt);
-    if (report(k + 1, found, delta, nev)) {
-      IPEPS_CUDA(cudaMemcpyAsync(A_dev, cur->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      IPEPS_CUDA(cudaStreamSynchronize(s));
-      return IPEPS_ERR_CANCELLED;
-    }
+  } catch (...) {
+    finish();
+    throw;
   }
-  IPEPS_CUDA(cudaMemcpyAsync(A_dev, cur->x.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  finish();
   return IPEPS_OK;
 }
 

@@ -371,3 +371,118 @@ def energy_fn(A, ham, chi, tol=1e-10, maxit=500, prec=FP64, state=None):
     tensor (Lx, Ly, d, D, D, D, D).  state: a dict that keeps the environment
     between calls for warm starts (a fresh dict each call cold-starts)."""
     return EnergyFunction.apply(A, ham, chi, tol, maxit, prec, {} if state is None else state)
+
+
+# ------------------------------------------------------------------ serving
+class ServerOpts(C.Structure):
+    _fields_ = [("slots", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("autotune", C.c_int)]
+
+
+class JobDesc(C.Structure):
+    _fields_ = [("shape", Shape), ("A_host", C.POINTER(C.c_double)), ("ham", C.c_void_p), ("opts", Opts)]
+
+
+class JobResult(C.Structure):
+    _fields_ = [("state", C.c_int), ("iterations", C.c_int), ("E", C.c_double), ("gnorm", C.c_double),
+                ("queued_ms", C.c_double), ("run_ms", C.c_double), ("iter_ms_p50", C.c_double),
+                ("iter_ms_p99", C.c_double), ("footprint_bytes", C.c_size_t), ("error", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("jobs_done", C.c_int), ("jobs_running", C.c_int), ("jobs_queued", C.c_int),
+                ("iterations", C.c_int64), ("iter_ms_p50", C.c_double), ("iter_ms_p99", C.c_double),
+                ("hbm_in_use_bytes", C.c_size_t), ("hbm_budget_bytes", C.c_size_t)]
+
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed", 4: "cancelled"}
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_ready", False):
+        vp, u64 = C.c_void_p, C.c_uint64
+        L.ipeps_server_opts_default.argtypes = [C.POINTER(ServerOpts)]
+        L.ipeps_job_footprint.argtypes = [C.POINTER(Shape), C.c_int]
+        L.ipeps_job_footprint.restype = C.c_size_t
+        L.ipeps_server_create.argtypes = [C.POINTER(ServerOpts), C.POINTER(vp)]
+        L.ipeps_server_submit.argtypes = [vp, C.POINTER(JobDesc), C.POINTER(u64)]
+        L.ipeps_server_poll.argtypes = [vp, u64, C.POINTER(JobResult)]
+        L.ipeps_server_wait.argtypes = [vp, u64, C.c_double]
+        L.ipeps_server_cancel.argtypes = [vp, u64]
+        L.ipeps_server_tensor.argtypes = [vp, u64, C.POINTER(C.c_double), C.c_size_t]
+        L.ipeps_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.ipeps_server_destroy.argtypes = [vp]
+        L.ipeps_server_last_error.restype = C.c_char_p
+        for name in ("ipeps_server_create", "ipeps_server_submit", "ipeps_server_poll", "ipeps_server_wait",
+                     "ipeps_server_cancel", "ipeps_server_tensor", "ipeps_server_get_stats"):
+            getattr(L, name).restype = C.c_int
+        L._server_ready = True
+    return L
+
+
+def _scheck(st):
+    if st != 0:
+        raise IpepsError(st, _server_lib().ipeps_server_last_error().decode())
+    return st
+
+
+def job_footprint(Lx, Ly, d, D, chi):
+    """Device bytes the server budgets for one job of this shape."""
+    sh = Shape(Lx, Ly, d, D)
+    return int(_server_lib().ipeps_job_footprint(C.byref(sh), chi))
+
+
+class Server:
+    """Many optimisation jobs on the current GPU (see ipeps_server_* in include/ipeps.h)."""
+
+    def __init__(self, slots=3, hbm_budget_bytes=0, autotune=True):
+        L = _server_lib()
+        o = ServerOpts()
+        L.ipeps_server_opts_default(C.byref(o))
+        o.slots, o.hbm_budget_bytes, o.autotune = slots, int(hbm_budget_bytes), int(bool(autotune))
+        self.h = C.c_void_p()
+        _scheck(L.ipeps_server_create(C.byref(o), C.byref(self.h)))
+        self.shapes = {}
+
+    def submit(self, A, ham, opts):
+        """A: host array (Lx, Ly, d, D, D, D, D); ham: Ham; opts: Opts.  Returns a job id."""
+        A = np.ascontiguousarray(np.asarray(A, dtype=np.float64))
+        desc = JobDesc(_shape(A), A.ctypes.data_as(C.POINTER(C.c_double)), ham.h, opts)
+        jid = C.c_uint64()
+        _scheck(_server_lib().ipeps_server_submit(self.h, C.byref(desc), C.byref(jid)))
+        self.shapes[jid.value] = A.shape
+        return jid.value
+
+    def poll(self, job):
+        r = JobResult()
+        _scheck(_server_lib().ipeps_server_poll(self.h, job, C.byref(r)))
+        return dict(state=JOB_STATES[r.state], iterations=r.iterations, E=r.E, gnorm=r.gnorm,
+                    queued_ms=r.queued_ms, run_ms=r.run_ms, iter_ms_p50=r.iter_ms_p50,
+                    iter_ms_p99=r.iter_ms_p99, footprint_bytes=r.footprint_bytes, error=r.error)
+
+    def wait(self, job, timeout=3600.0):
+        _scheck(_server_lib().ipeps_server_wait(self.h, job, float(timeout)))
+        return self.poll(job)
+
+    def cancel(self, job):
+        _scheck(_server_lib().ipeps_server_cancel(self.h, job))
+
+    def tensor(self, job):
+        out = np.zeros(self.shapes[job])
+        _scheck(_server_lib().ipeps_server_tensor(self.h, job, out.ctypes.data_as(C.POINTER(C.c_double)),
+                                                  out.size))
+        return out
+
+    def stats(self):
+        s = ServerStats()
+        _scheck(_server_lib().ipeps_server_get_stats(self.h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            _server_lib().ipeps_server_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        if _lib is not None:
+            self.close()

@@ -3,7 +3,7 @@ whose oracle run takes minutes (so that the GPU suite does not repeat it).
 Every number comes from oracle/ (FP64, CPU) on inputs from the seeded
 generators; nothing here calls the CUDA path.
 
-  python tests/golden/make_golden.py rangefinder   # D=4, chi=68 truncated-SVD case
+  python tests/golden/make_golden.py rangefinder   # D=5, chi=44 truncated-SVD case
   python tests/golden/make_golden.py lbfgs         # plain (5) and preconditioned (3) L-BFGS iterations
 """
 import json
@@ -34,18 +34,20 @@ def _write(name, rec):
 
 
 def rangefinder():
-    """Heisenberg 1x1 (rotated), random D=4 tensor (uniform seed 3), chi=68: the
-    four-corner product is 1088 x 1088, beyond the size where the GPU path cold
-    starts its projector SVD from a random range finder."""
-    chi, seed, tol = 68, 3, 1e-11
-    cell = inputs.uniform_cell(1, 1, 2, 4, seed)
+    """Heisenberg 1x1 (rotated), random D=5 tensor (uniform seed 3), chi=44: the
+    four-corner product is 1100 x 1100, beyond the size where the GPU path cold
+    starts its projector SVD from a random range finder, and its cut is
+    resolvable (relative gap (s_chi - s_chi+1) / s_1 about 1.8e-8)."""
+    D, chi, seed, tol = 5, 44, 3, 1e-11
+    cell = inputs.uniform_cell(1, 1, 2, D, seed)
     t0 = time.time()
     E, g, info = OG.energy_and_gradient(cell, OM.heisenberg(True), chi, tol=tol, maxit=800, return_info=True)
     gap = min(OC.cut_gaps(1, 1, OC.as_torch_cell(cell), info["env"], chi))
-    _write(f"rangefinder_d4_chi{chi}.json",
-           {"case": "uniform_cell(1, 1, 2, 4, seed=3), Heisenberg rotated", "chi": chi, "ctm_tol": tol, "E": E,
-            "grad": g[0][0].ravel().tolist(), "min_cut_gap": gap, "ctm_iters": info["ctm_iters"],
-            "adjoint_residual": info["adjoint_residual"], "seconds": time.time() - t0})
+    _write(f"rangefinder_d{D}_chi{chi}.json",
+           {"case": f"uniform_cell(1, 1, 2, {D}, seed={seed}), Heisenberg rotated", "D": D, "chi": chi,
+            "seed": seed, "ctm_tol": tol, "E": E, "grad": g[0][0].ravel().tolist(), "min_cut_gap": gap,
+            "ctm_iters": info["ctm_iters"], "adjoint_residual": info["adjoint_residual"],
+            "seconds": time.time() - t0})
 
 
 def lbfgs():

@@ -61,3 +61,16 @@ def test_nnn_setter_host_logic(lib):
     st = ipeps.lib().ipeps_ham_set_nnn(None, None, None)
     assert st == 1 and b"NULL" in ipeps.lib().ipeps_last_error()
     del h
+
+
+def test_job_footprint_host_logic(lib):
+    # the server's admission estimate grows with (chi D^2)^2 and the cell size;
+    # invalid shapes give 0
+    from paper_2511_09546_gb300 import ipeps
+
+    a = ipeps.job_footprint(1, 1, 2, 4, 32)
+    b = ipeps.job_footprint(1, 1, 2, 4, 64)
+    c = ipeps.job_footprint(2, 2, 2, 4, 64)
+    assert 0 < a < b < c
+    assert 3.0 < (b - (64 << 20)) / (a - (64 << 20)) < 4.5
+    assert ipeps.job_footprint(0, 1, 2, 4, 64) == 0
