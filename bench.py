@@ -581,6 +581,115 @@ def run_ttt(args):
     print(json.dumps(out), flush=True)
 
 
+def run_serve(args):
+    """--mode serve: the serving mix.  Jobs arrive as a seeded Poisson stream
+    (mean gap 50 ms): J1-J2 Heisenberg with J2 ~ U[0, 0.6], D ~ U{2 .. --serve-dmax},
+    chi = 2 D^2 or 4 D^2, 1x1 (sublattice-rotated) or 2x2 cell, A ~ U[-1, 1];
+    each job runs --serve-iters preconditioned L-BFGS iterations in --prec (default
+    bf16x3) on the server's slots.  Reports per-iteration p50/p99 latency, job
+    throughput and time from submission to completion."""
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import inputs, ipeps
+
+    rng = np.random.default_rng(0)
+    prec = _prec(ipeps, args.prec if args.prec != "fp64_tc" else "bf16x3")
+    specs = []
+    t = 0.0
+    for k in range(args.serve_jobs):
+        t += rng.exponential(0.05)
+        D = int(rng.integers(2, args.serve_dmax + 1))
+        chi = int(D * D * (2 if rng.random() < 0.5 else 4))
+        cell = (1, 1) if rng.random() < 0.5 else (2, 2)
+        J2 = float(rng.uniform(0.0, 0.6))
+        A = ipeps.cell_tensor(inputs.uniform_cell(cell[0], cell[1], 2, D, 1000 + k))
+        specs.append((t, D, chi, cell, J2, A))
+    srv = ipeps.Server(slots=args.serve_slots)
+    clocks = Clocks(0)
+    t0 = time.perf_counter()
+    ids = []
+    for (ta, D, chi, cell, J2, A) in specs:
+        while time.perf_counter() - t0 < ta:
+            time.sleep(0.001)
+        ham = ipeps.ham_j1j2(1.0, J2, rotated=(cell == (1, 1)))
+        o = ipeps.default_opts(chi=chi, maxiter=args.serve_iters, precondition=1, ctm_tol=1e-10, ctm_maxit=300,
+                               prec=prec)
+        ids.append((srv.submit(A, ham, o), ta, D, chi, cell))
+    res = []
+    for j, ta, D, chi, cell in ids:
+        r = srv.wait(j, 7200)
+        res.append(dict(r, D=D, chi=chi, cell=f"{cell[0]}x{cell[1]}", total_ms=r["queued_ms"] + r["run_ms"]))
+        print(f"[serve] job {j} D={D} chi={chi} cell={cell} {r['state']} it={r['iterations']} E={r['E']:.10f} "
+              f"queued {r['queued_ms']:.0f} ms run {r['run_ms']:.0f} ms", file=sys.stderr, flush=True)
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    done = [r for r in res if r["state"] == "done"]
+    its = sum(r["iterations"] for r in done)
+    rec = {"mode": "serve", "precision": args.prec, "jobs": len(res), "done": len(done), "slots": args.serve_slots,
+           "iterations_per_job": args.serve_iters, "wall_s": wall, "jobs_per_s": len(done) / wall,
+           "iterations_per_s": its / wall,
+           "iter_latency_ms": {"p50": st["iter_ms_p50"], "p99": st["iter_ms_p99"]},
+           "job_latency_ms": {"p50": float(np.percentile([r["total_ms"] for r in done], 50)) if done else None,
+                              "p99": float(np.percentile([r["total_ms"] for r in done], 99)) if done else None},
+           "mix": f"Poisson arrivals (mean gap 50 ms, seed 0), D in 2..{args.serve_dmax}, chi in {{2D^2, 4D^2}}, "
+                  "1x1 / 2x2, J2 ~ U[0, 0.6]",
+           "clocks": clocks.stop(), "failed": [r for r in res if r["state"] != "done"]}
+    print(json.dumps(rec), flush=True)
+
+
+def run_fdcheck(args):
+    """--mode fdcheck: the fixed-point gradient of the workload (default the Kitaev
+    1x2, d=4, D=6, chi=72 cell) against central differences of the energy
+    (step 1e-6) on 32 entries drawn by seed 1, everything on the GPU in --prec."""
+    import torch
+
+    import __graft_entry__ as entry
+
+    entry.build()
+    from paper_2511_09546_gb300 import inputs, ipeps
+
+    w = inputs.WORKLOADS[args.workload]
+    A = torch.as_tensor(ipeps.cell_tensor(w["gen"]()), device="cuda")
+    ham = _ham(ipeps, w)
+    prec = _prec(ipeps, args.prec)
+    tol = 1e-11
+    t0 = time.perf_counter()
+    env, it, err = ipeps.ctmrg(A, w["chi"], tol=tol, maxit=1000, prec=prec)
+    t_ctm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    E, g = ipeps.energy_grad(A, env, ham)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    idx = inputs.random_entries(A.numel(), 32, seed=1)
+    h = 1e-6
+    gflat = g.view(-1).cpu().numpy()
+    rows = []
+    t0 = time.perf_counter()
+    for i in idx:
+        vals = []
+        for sgn in (1, -1):
+            Ap = A.clone()
+            Ap.view(-1)[int(i)] += sgn * h
+            env, _, _ = ipeps.ctmrg(Ap, w["chi"], tol=tol, maxit=1000, prec=prec, env=env)
+            vals.append(ipeps.energy(Ap, env, ham))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        rows.append((int(i), float(gflat[i]), fd))
+        print(f"[fd] entry {i}: grad {gflat[i]: .10e} fd {fd: .10e} diff {fd - gflat[i]: .2e}", file=sys.stderr,
+              flush=True)
+    gmax = float(np.abs(gflat).max())
+    diffs = [abs(fd - gi) for _, gi, fd in rows]
+    rec = {"mode": "fdcheck", "workload": args.workload, "precision": args.prec, "E": E, "ctm_iters": it,
+           "ctm_change": err, "seconds_ctmrg": t_ctm, "seconds_gradient": t_grad,
+           "seconds_fd": time.perf_counter() - t0, "entries": len(rows), "step": h,
+           "max_abs_diff": max(diffs), "max_abs_grad": gmax, "max_rel_diff_vs_max_grad": max(diffs) / gmax,
+           "rows": rows}
+    print(json.dumps(rec), flush=True)
+
+
 def run_gemm(args):
     """--mode gemm: one tensor-core GEMM (3xTF32, or the BF16-digit kernel for
     --prec fp64_tc / bf16x3) on n x n x n FP64 operands, timed per kernel class
@@ -638,7 +747,11 @@ def main():
     ap.add_argument("--prec", default="fp64_tc", choices=PRECS)
     ap.add_argument("--workload", default="heis_d4_chi64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="pass", choices=["pass", "optimize", "gemm", "ctmrg", "ttt"])
+    ap.add_argument("--mode", default="pass", choices=["pass", "optimize", "gemm", "ctmrg", "ttt", "serve", "fdcheck"])
+    ap.add_argument("--serve-jobs", type=int, default=64)
+    ap.add_argument("--serve-dmax", type=int, default=6)
+    ap.add_argument("--serve-iters", type=int, default=3)
+    ap.add_argument("--serve-slots", type=int, default=3)
     ap.add_argument("--ttt-maxiter", type=int, default=400)
     ap.add_argument("--ttt-plain-seconds", type=float, default=1200.0)
     ap.add_argument("--gemm-n", type=int, default=8192)
@@ -647,7 +760,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    modes = {"optimize": run_optimize, "gemm": run_gemm, "ctmrg": run_ctmrg, "ttt": run_ttt}
+    modes = {"optimize": run_optimize, "gemm": run_gemm, "ctmrg": run_ctmrg, "ttt": run_ttt, "serve": run_serve,
+             "fdcheck": run_fdcheck}
     if args.mode in modes:
         modes[args.mode](args)
         return

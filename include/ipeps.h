@@ -333,6 +333,9 @@ ipeps_status ipeps_gemm_noalloc(int ta, int tb, int64_t M, int64_t N, int64_t K,
 const char *ipeps_last_error(void);
 /* Kernel launches issued by this thread since the last reset (for reports). */
 uint64_t ipeps_launch_count(int reset);
+/* Host waits on a stream (synchronisations) issued by this thread since the
+ * last reset (for reports). */
+uint64_t ipeps_sync_count(int reset);
 /* Live kernel timing: enable != 0 clears the statistics and records a CUDA
  * event pair around every instrumented launch on its stream; 0 stops.
  * ipeps_profile_query fills the launch count, summed duration (ms) and the

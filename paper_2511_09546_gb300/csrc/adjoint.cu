@@ -30,7 +30,7 @@ double energy_only(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   int E = energy_on_tape(t, c, e.chi, sv, H, hd);
   double v;
   IPEPS_CUDA(cudaMemcpyAsync(&v, t.vp(E), sizeof(double), cudaMemcpyDeviceToHost, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   return v;
 }
 
@@ -43,7 +43,7 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   auto t0 = std::chrono::steady_clock::now();
   auto lap = [&](const char *what) {
     if (!dbg) return;
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     auto t1 = std::chrono::steady_clock::now();
     std::fprintf(stderr, "[ipeps] energy_grad %s: %.1f ms\n", what,
                  std::chrono::duration<double, std::milli>(t1 - t0).count());
@@ -100,7 +100,7 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
     nrm2(nenv, ebar.p, nb.p, s);
     double h;
     IPEPS_CUDA(cudaMemcpyAsync(&h, nb.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     std::fprintf(stderr, "[ipeps] |dE/denv| = %.6e\n", h);
   }
 
@@ -146,7 +146,7 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
     std::fprintf(stderr, "[ipeps] adjoint: %d matvecs, residual %.2e, fixed-point residual %.2e, cg %d\n", nmv,
                  rel, fpres, tF.svd_iters);
   vjp(lam.p, nullptr, grad);
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   if (adj_resid) *adj_resid = rel;
   if (adj_mv) *adj_mv = nmv;
   return E;

@@ -26,6 +26,16 @@ uint64_t &launch_counter() {
   return n;
 }
 
+uint64_t &sync_counter() {
+  static thread_local uint64_t n = 0;
+  return n;
+}
+
+cudaError_t stream_sync(cudaStream_t s) {
+  ++sync_counter();
+  return cudaStreamSynchronize(s);
+}
+
 void check_launch(const char *what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) throw Error(IPEPS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
@@ -135,6 +145,12 @@ const char *ipeps_profile_names(void) {
 uint64_t ipeps_launch_count(int reset) {
   uint64_t n = ipeps::launch_counter();
   if (reset) ipeps::launch_counter() = 0;
+  return n;
+}
+
+uint64_t ipeps_sync_count(int reset) {
+  uint64_t n = ipeps::sync_counter();
+  if (reset) ipeps::sync_counter() = 0;
   return n;
 }
 

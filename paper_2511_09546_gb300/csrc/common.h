@@ -37,6 +37,10 @@ uint64_t &launch_counter();
 inline void count_launch(uint64_t n = 1) { launch_counter() += n; }
 void check_launch(const char *what);
 
+// cudaStreamSynchronize that counts the host waits of this thread (reports)
+cudaError_t stream_sync(cudaStream_t s);
+uint64_t &sync_counter();
+
 // Stream-ordered device allocations (the pool keeps freed blocks cached).
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);

@@ -312,7 +312,7 @@ double spectra_change(const double *a, const double *b, int nmat, int chi, cudaS
   check_launch("spectra_diff");
   std::vector<double> h(nmat);
   IPEPS_CUDA(cudaMemcpyAsync(h.data(), d.p, nmat * sizeof(double), cudaMemcpyDeviceToHost, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   return *std::max_element(h.begin(), h.end());
 }
 
@@ -371,7 +371,7 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
         int bad = 0;
         count_nonfinite(e.total(), e.buf.p, cnt, s);
         IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-        IPEPS_CUDA(cudaStreamSynchronize(s));
+        IPEPS_CUDA(stream_sync(s));
         dev_free(cnt, s);
         if (bad) throw Error(IPEPS_ERR_NONFINITE, "CTMRG produced non-finite environment tensors");
       }
@@ -382,7 +382,7 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
             int x = i / c.Ly, y = i % c.Ly, bad = 0;
             count_nonfinite(n < 4 ? e.csize() : e.esize(), e.ptr(n, x, y), cnt, s);
             IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-            IPEPS_CUDA(cudaStreamSynchronize(s));
+            IPEPS_CUDA(stream_sync(s));
             if (bad) std::fprintf(stderr, "[ipeps] ctmrg it %d: tensor %d site %d has %d non-finite entries\n", it, n, i, bad);
           }
         dev_free(cnt, s);
@@ -457,7 +457,7 @@ DBuf solve_signs(const EnvImpl &ref, const std::vector<const double *> &cand, cu
     check_launch("overlap");
     std::vector<double> h(size_t(8) * ns * chi * chi);
     IPEPS_CUDA(cudaMemcpyAsync(h.data(), Wd.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     for (int k = 0; k < 8 * ns; ++k)
       W[k].assign(h.begin() + int64_t(k) * chi * chi, h.begin() + int64_t(k + 1) * chi * chi);
   }
@@ -529,7 +529,7 @@ DBuf solve_signs(const EnvImpl &ref, const std::vector<const double *> &cand, cu
   if (residual) *residual = res;
   DBuf out(hs.size(), s);
   IPEPS_CUDA(cudaMemcpyAsync(out.p, hs.data(), hs.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   return out;
 }
 

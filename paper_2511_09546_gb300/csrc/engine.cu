@@ -154,7 +154,7 @@ void Tape::backward() {
         if (!vars[v].grad.p) continue;
         count_nonfinite(vars[v].val.size(), vars[v].grad.p, cnt, s);
         IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-        IPEPS_CUDA(cudaStreamSynchronize(s));
+        IPEPS_CUDA(stream_sync(s));
         if (bad) std::fprintf(stderr, "[ipeps] non-finite cotangent after node %d (%s), var %zu\n", idx,
                               typeid(**it).name(), v);
       }
@@ -400,7 +400,7 @@ struct RhoRatioNode : Node {
       IPEPS_CUDA(cudaMemcpyAsync(hv + 1, den.p, 8, cudaMemcpyDeviceToHost, t.s));
       IPEPS_CUDA(cudaMemcpyAsync(hv + 2, t.vp(out), 8, cudaMemcpyDeviceToHost, t.s));
       IPEPS_CUDA(cudaMemcpyAsync(hv + 3, go, 8, cudaMemcpyDeviceToHost, t.s));
-      IPEPS_CUDA(cudaStreamSynchronize(t.s));
+      IPEPS_CUDA(stream_sync(t.s));
       std::fprintf(stderr, "[ipeps] rho_ratio num %.6e den %.6e out %.6e gout %.6e d %d two %d\n", hv[0], hv[1],
                    hv[2], hv[3], d, int(two));
     }
@@ -526,7 +526,7 @@ void svd_full(const double *M, int64_t N, double *U, double *S, double *V, cudaS
   count_launch();
   std::vector<double> hs(N);
   IPEPS_CUDA(cudaMemcpyAsync(hs.data(), sig.p, N * sizeof(double), cudaMemcpyDeviceToHost, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   std::vector<int> perm(N);
   std::iota(perm.begin(), perm.end(), 0);
   std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hs[a] > hs[b]; });
@@ -538,7 +538,7 @@ void svd_full(const double *M, int64_t N, double *U, double *S, double *V, cudaS
   svd_gather_kernel<<<512, 256, 0, s>>>(G.p, Vg.p, sig.p, dperm, N, U, V);
   count_launch();
   check_launch("svd_gather");
-  IPEPS_CUDA(cudaStreamSynchronize(s));  // host vectors above go out of scope
+  IPEPS_CUDA(stream_sync(s));  // host vectors above go out of scope
   dev_free(dperm, s);
 }
 
@@ -674,7 +674,7 @@ void t_svd(Tape &t, int M, int k, int *U, int *S, int *V) {
       if (!warm) vc = DBuf(csz, t.s);
       IPEPS_CUDA(cudaMemcpyAsync(vc.p, Vb.p, N * kb * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
       IPEPS_CUDA(cudaMemcpyAsync(vc.p + N * kb, Sb.p, kb * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
-      IPEPS_CUDA(cudaStreamSynchronize(t.s));
+      IPEPS_CUDA(stream_sync(t.s));
     }
     svd_sign_kernel<<<unsigned(k), 256, 0, t.s>>>(Ub.p, Vb.p, N, kb);
     *U = t.make({N, int64_t(k)});
@@ -686,7 +686,7 @@ void t_svd(Tape &t, int M, int k, int *U, int *S, int *V) {
     check_launch("t_svd block");
     IPEPS_CUDA(cudaMemcpyAsync(t.vp(*S), Sb.p, k * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
     if (t.record) push_trunc_svd_node(t, M, *U, *S, *V, N, k, int(kb), std::move(Ub), std::move(Sb), std::move(Vb));
-    else IPEPS_CUDA(cudaStreamSynchronize(t.s));
+    else IPEPS_CUDA(stream_sync(t.s));
     return;
   }
   auto *nd = new SVDNode;

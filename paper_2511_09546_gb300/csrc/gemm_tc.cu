@@ -405,10 +405,10 @@ void tc_check_errors(cudaStream_t s) {
   int *w = tc_error_word();
   int h = 0;
   IPEPS_CUDA(cudaMemcpyAsync(&h, w, sizeof(int), cudaMemcpyDeviceToHost, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   if (h) {
     IPEPS_CUDA(cudaMemsetAsync(w, 0, sizeof(int), s));
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     throw Error(IPEPS_ERR_TIMEOUT, "a tensor-core GEMM's bounded mbarrier wait expired");
   }
 }

@@ -45,7 +45,7 @@ double ddot(int64_t n, const double *a, const double *b, cudaStream_t s) {
   dot(n, a, b, r.p, s);
   double h;
   IPEPS_CUDA(cudaMemcpyAsync(&h, r.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   return h;
 }
 
@@ -68,7 +68,7 @@ double absmax(int64_t n, const double *x, cudaStream_t s) {
   count_launch();
   double h;
   IPEPS_CUDA(cudaMemcpyAsync(&h, r.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   return h;
 }
 
@@ -364,7 +364,7 @@ ipeps_status optimize_impl(const Cell &c, double *A_dev, const HamImpl &H, const
   ipeps_iter_info info = run.start(A_dev);
   auto finish = [&]() {
     run.copy_tensor(A_dev);
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
   };
   if (cb && cb(&info, user)) {
     finish();

@@ -70,15 +70,18 @@ void local_metrics(const EnvImpl &e, const double *A_dev, DBuf &Mall, cudaStream
 
 double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int krylov, int restarts,
                  double rtol, cudaStream_t s, int *matvecs) {
+  // Arnoldi with classical Gram-Schmidt applied twice, all on the device; the
+  // new Hessenberg column (j + 2 numbers) comes back to the host once per
+  // step for the Givens rotations and the residual estimate
   IPEPS_REQUIRE(krylov >= 1 && restarts >= 1, "gmres: krylov and restarts must be >= 1");
   const int m = krylov;
-  DBuf V(size_t(m + 1) * n, s), w(size_t(n), s), r(size_t(n), s), h(size_t(m + 1), s),
+  DBuf V(size_t(m + 1) * n, s), w(size_t(n), s), r(size_t(n), s), h(size_t(m + 2), s), h2(size_t(m + 2), s),
       sc(1, s);
   fill(x, n, 0.0, s);
   auto host_scalar = [&](const double *p) {
     double v;
     IPEPS_CUDA(cudaMemcpyAsync(&v, p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     return v;
   };
   nrm2(n, b, sc.p, s);
@@ -89,6 +92,7 @@ double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int kr
     return 0.0;
   }
   double rel = 1.0;
+  std::vector<double> col(size_t(m) + 2);
   for (int cycle = 0; cycle < restarts; ++cycle) {
     if (cycle == 0) {
       IPEPS_CUDA(cudaMemcpyAsync(r.p, b, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -109,18 +113,20 @@ double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int kr
     for (int j = 0; j < m; ++j) {
       mv(V.p + int64_t(j) * n, w.p);
       ++nmv;
-      std::vector<double> hh(j + 1, 0.0), h2(j + 1);
-      for (int pass = 0; pass < 2; ++pass) {
-        // h = V[0..j] w ; w -= V[0..j]^T h
-        gemm_f64(false, false, j + 1, 1, n, 1.0, V.p, n, w.p, 1, 0.0, h.p, 1, s);
-        gemm_f64(true, false, n, 1, j + 1, -1.0, V.p, n, h.p, 1, 1.0, w.p, 1, s);
-        IPEPS_CUDA(cudaMemcpyAsync(h2.data(), h.p, (j + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
-        IPEPS_CUDA(cudaStreamSynchronize(s));
-        for (int i = 0; i <= j; ++i) hh[i] += h2[i];
-      }
-      nrm2(n, w.p, sc.p, s);
-      double hn = host_scalar(sc.p);
-      for (int i = 0; i <= j; ++i) H[i * m + j] = hh[i];
+      // h = V[0..j] w, w -= V[0..j]^T h, twice; h accumulates both passes
+      gemm_f64(false, false, j + 1, 1, n, 1.0, V.p, n, w.p, 1, 0.0, h.p, 1, s);
+      gemm_f64(true, false, n, 1, j + 1, -1.0, V.p, n, h.p, 1, 1.0, w.p, 1, s);
+      gemm_f64(false, false, j + 1, 1, n, 1.0, V.p, n, w.p, 1, 0.0, h2.p, 1, s);
+      gemm_f64(true, false, n, 1, j + 1, -1.0, V.p, n, h2.p, 1, 1.0, w.p, 1, s);
+      axpy(j + 1, 1.0, h2.p, h.p, s);
+      nrm2(n, w.p, h.p + j + 1, s);
+      // next basis vector (a zero norm leaves it zero; the loop stops below)
+      IPEPS_CUDA(cudaMemcpyAsync(V.p + int64_t(j + 1) * n, w.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      div_by_scalar(n, V.p + int64_t(j + 1) * n, h.p + j + 1, s);
+      IPEPS_CUDA(cudaMemcpyAsync(col.data(), h.p, size_t(j + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      IPEPS_CUDA(stream_sync(s));
+      const double hn = col[j + 1];
+      for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
       H[(j + 1) * m + j] = hn;
       for (int i = 0; i < j; ++i) {
         double t = cs[i] * H[i * m + j] + sn[i] * H[(i + 1) * m + j];
@@ -144,9 +150,6 @@ double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int kr
         tlast = tn;
       }
       if (rel <= rtol || hn == 0.0) break;
-      IPEPS_CUDA(cudaMemcpyAsync(V.p + int64_t(j + 1) * n, w.p, n * sizeof(double),
-                                 cudaMemcpyDeviceToDevice, s));
-      scal(n, 1.0 / hn, V.p + int64_t(j + 1) * n, s);
     }
     std::vector<double> y(used, 0.0);
     for (int i = used - 1; i >= 0; --i) {
@@ -156,7 +159,7 @@ double gmres_dev(int64_t n, const MatVec &mv, const double *b, double *x, int kr
     }
     IPEPS_CUDA(cudaMemcpyAsync(h.p, y.data(), used * sizeof(double), cudaMemcpyHostToDevice, s));
     gemm_f64(true, false, n, 1, used, 1.0, V.p, n, h.p, 1, 1.0, x, 1, s);
-    IPEPS_CUDA(cudaStreamSynchronize(s));  // y leaves scope
+    IPEPS_CUDA(stream_sync(s));  // y leaves scope
     if (rel <= rtol) break;
   }
   if (matvecs) *matvecs = nmv;

@@ -251,7 +251,7 @@ int jacobi_svd_colmajor(double *G, int64_t m, int64_t n, double *V, cudaStream_t
     check_launch("jacobi_pair");
     double h = 0.0;
     IPEPS_CUDA(cudaMemcpyAsync(&h, off.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     if (!(h > tol)) break;
   }
   // copy back the first n columns (padded columns never mix with real ones)

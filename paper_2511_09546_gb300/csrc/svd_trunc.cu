@@ -219,7 +219,7 @@ bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, dou
       residual_kernel<<<unsigned(chi), 256, 0, s>>>(Y.p, U, S, N, k, res.p);
       count_launch();
       IPEPS_CUDA(cudaMemcpyAsync(hr.data(), res.p, chi * sizeof(double), cudaMemcpyDeviceToHost, s));
-      IPEPS_CUDA(cudaStreamSynchronize(s));
+      IPEPS_CUDA(stream_sync(s));
       double worst = 0.0;
       if (tc) {
         // products carry ~1e-6 |M| of noise: converged once every residual is at that floor
@@ -250,7 +250,7 @@ bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, dou
     colnorm_colmajor<<<unsigned(k), 256, 0, s>>>(Rz.p, k, sig.p);
     count_launch();
     IPEPS_CUDA(cudaMemcpyAsync(hs.data(), sig.p, k * sizeof(double), cudaMemcpyDeviceToHost, s));
-    IPEPS_CUDA(cudaStreamSynchronize(s));
+    IPEPS_CUDA(stream_sync(s));
     std::iota(perm.begin(), perm.end(), 0);
     std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hs[a] > hs[b]; });
     for (int i = 0; i < k; ++i) sorted[i] = hs[perm[i]];
@@ -278,7 +278,7 @@ bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, dou
     IPEPS_CUDA(cudaMemcpyAsync(cache, Vc.p, size_t(N) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
     IPEPS_CUDA(cudaMemcpyAsync(cache + N * k, Sc.p, size_t(k) * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  IPEPS_CUDA(cudaStreamSynchronize(s));
+  IPEPS_CUDA(stream_sync(s));
   dev_free(dflag, s);
   dev_free(dperm, s);
   if (iters) *iters = it;
@@ -351,6 +351,28 @@ __global__ void col_xpby_kernel(int64_t rows, int n, const double *f, const doub
   for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < rows * n;
        e += int64_t(gridDim.x) * blockDim.x)
     P[e] = R[e] + f[e % n] * P[e];
+}
+
+// two pinned host buffers and events per thread for lagged residual checks
+struct PinnedSlots {
+  double *buf = nullptr;
+  int cap = 0;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double *slot(int i) { return buf + size_t(i) * cap; }
+};
+
+PinnedSlots &pinned_slots(int n) {
+  static thread_local PinnedSlots p;
+  if (!p.ev[0]) {
+    IPEPS_CUDA(cudaEventCreateWithFlags(&p.ev[0], cudaEventDisableTiming));
+    IPEPS_CUDA(cudaEventCreateWithFlags(&p.ev[1], cudaEventDisableTiming));
+  }
+  if (p.cap < n) {
+    if (p.buf) cudaFreeHost(p.buf);
+    p.cap = std::max(n, 256);
+    IPEPS_CUDA(cudaMallocHost(&p.buf, size_t(2) * p.cap * sizeof(double)));
+  }
+  return p;
 }
 
 void col_axpy(int64_t rows, int n, double sgn, const double *f, const double *X, double *Y, cudaStream_t s) {
@@ -442,22 +464,20 @@ struct TruncSVDNode : Node {
     IPEPS_CUDA(cudaMemcpyAsync(P.p, R.p, 2 * n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
     coldot(2 * n, c, G.p, G.p, bb.p, s);
     coldot(2 * n, c, R.p, R.p, rr.p, s);
-    std::vector<double> hb(c), hr(c);
+    std::vector<double> hb(c);
     IPEPS_CUDA(cudaMemcpyAsync(hb.data(), bb.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
-    // stop at 1e-12 relative, or when the residual stagnates at the rounding
-    // floor of the small singular values (K is applied through M, whose
-    // rounding is eps |M| against s_i |x|)
+    // Residuals come back through two pinned slots, one iteration late: the
+    // host checks iteration i while the device already runs iteration i + 1,
+    // so the stream never drains for the check (a converged run does one
+    // extra CG step).  Stop at 1e-12 relative, or when the residual stagnates
+    // at the rounding floor of the small singular values (K is applied
+    // through M, whose rounding is eps |M| against s_i |x|).
+    PinnedSlots &pin = pinned_slots(c);
+    IPEPS_CUDA(cudaMemcpyAsync(pin.slot(0), rr.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+    IPEPS_CUDA(cudaEventRecord(pin.ev[0], s));
     std::vector<double> hist;
     for (int it = 0; it < 100; ++it) {
-      IPEPS_CUDA(cudaMemcpyAsync(hr.data(), rr.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
-      IPEPS_CUDA(cudaStreamSynchronize(s));
-      double worst = 0.0;
-      for (int i = 0; i < c; ++i)
-        if (hb[i] > 0.0) worst = std::max(worst, std::sqrt(hr[i] / hb[i]));
-      t.svd_iters += 1;
-      hist.push_back(worst);
-      if (worst <= 1e-12) break;
-      if (hist.size() > 4 && worst > 0.5 * hist[hist.size() - 4]) break;
+      // enqueue the step that produces residual it + 1
       K(P.p, KP.p);
       coldot(2 * n, c, P.p, KP.p, pk.p, s);
       ratio_kernel<<<(c + 127) / 128, 128, 0, s>>>(rr.p, pk.p, c, al.p);
@@ -470,6 +490,20 @@ struct TruncSVDNode : Node {
       col_xpby_kernel<<<512, 256, 0, s>>>(2 * n, c, al.p, R.p, P.p);
       count_launch();
       std::swap(rr, rn);
+      const int nxt = (it + 1) & 1;
+      IPEPS_CUDA(cudaMemcpyAsync(pin.slot(nxt), rr.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
+      IPEPS_CUDA(cudaEventRecord(pin.ev[nxt], s));
+      // check residual it
+      IPEPS_CUDA(cudaEventSynchronize(pin.ev[it & 1]));
+      ++sync_counter();
+      const double *hr = pin.slot(it & 1);
+      double worst = 0.0;
+      for (int i = 0; i < c; ++i)
+        if (hb[i] > 0.0) worst = std::max(worst, std::sqrt(hr[i] / hb[i]));
+      t.svd_iters += 1;
+      hist.push_back(worst);
+      if (worst <= 1e-12) break;
+      if (hist.size() > 4 && worst > 0.5 * hist[hist.size() - 4]) break;
     }
     check_launch("trunc_svd_bwd");
     // gM += X V^T + U Y^T

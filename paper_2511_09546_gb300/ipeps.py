@@ -60,6 +60,8 @@ def lib():
         L.ipeps_last_error.restype = C.c_char_p
         L.ipeps_launch_count.restype = C.c_uint64
         L.ipeps_launch_count.argtypes = [i]
+        L.ipeps_sync_count.restype = C.c_uint64
+        L.ipeps_sync_count.argtypes = [i]
         L.ipeps_profile.argtypes = [i]
         L.ipeps_profile_query.argtypes = [C.c_char_p, C.POINTER(C.c_uint64), dp, dp, dp]
         L.ipeps_profile_query.restype = i
@@ -273,6 +275,11 @@ def optimize(A, ham, opts, callback=None):
 
 def launch_count(reset=False):
     return int(lib().ipeps_launch_count(1 if reset else 0))
+
+
+def sync_count(reset=False):
+    """Host waits on a stream issued by this thread (since the last reset)."""
+    return int(lib().ipeps_sync_count(1 if reset else 0))
 
 
 def profile(enable=True):
