@@ -305,13 +305,15 @@ void corner_spectra(EnvImpl &e, cudaStream_t s) {
   e.have_spectra = true;
 }
 
-double spectra_change(const double *a, const double *b, int nmat, int chi, cudaStream_t s) {
+double spectra_change(const double *a, const double *b, int nmat, int chi, cudaStream_t s, const int *count_dev,
+                      int *count_host) {
   DBuf d(size_t(nmat), s);
   spectra_diff_kernel<<<nmat, 256, 0, s>>>(a, b, chi, d.p);
   count_launch();
   check_launch("spectra_diff");
   std::vector<double> h(nmat);
   IPEPS_CUDA(cudaMemcpyAsync(h.data(), d.p, nmat * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (count_dev) IPEPS_CUDA(cudaMemcpyAsync(count_host, count_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
   IPEPS_CUDA(stream_sync(s));
   return *std::max_element(h.begin(), h.end());
 }
@@ -323,6 +325,8 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
   const int nmat = 4 * c.nsites();
   if (!e.have_spectra) corner_spectra(e, s);
   DBuf prev(size_t(nmat) * e.chi, s);
+  DBuf bad_buf(1, s);
+  int *bad_dev = reinterpret_cast<int *>(bad_buf.p);
   double change = INFINITY;
   // split precision: 3xTF32 iterations while the change is above the split
   // floor and still improving, then (TF32X3) FP64 iterations down to tol
@@ -366,15 +370,8 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
                                      cudaMemcpyDeviceToDevice, s));
         }
       std::swap(e.buf, nb);
-      {
-        int *cnt = static_cast<int *>(dev_alloc(sizeof(int), s));
-        int bad = 0;
-        count_nonfinite(e.total(), e.buf.p, cnt, s);
-        IPEPS_CUDA(cudaMemcpyAsync(&bad, cnt, sizeof(int), cudaMemcpyDeviceToHost, s));
-        IPEPS_CUDA(stream_sync(s));
-        dev_free(cnt, s);
-        if (bad) throw Error(IPEPS_ERR_NONFINITE, "CTMRG produced non-finite environment tensors");
-      }
+      // non-finite entries are counted on the device and read with the spectra change below
+      count_nonfinite(e.total(), e.buf.p, bad_dev, s);
       if (std::getenv("IPEPS_DEBUG_NAN")) {
         int *cnt = static_cast<int *>(dev_alloc(sizeof(int), s));
         for (int n = 0; n < 8; ++n)
@@ -389,7 +386,9 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
       }
     }
     corner_spectra(e, s);
-    change = spectra_change(prev.p, e.spectra.p, nmat, e.chi, s);
+    int bad = 0;
+    change = spectra_change(prev.p, e.spectra.p, nmat, e.chi, s, bad_dev, &bad);
+    if (bad) throw Error(IPEPS_ERR_NONFINITE, "CTMRG produced non-finite environment tensors");
     if (!std::isfinite(change)) throw Error(IPEPS_ERR_NONFINITE, "CTMRG produced non-finite values");
     if (change < tol && it >= 2) break;
     if (change < 0.7 * best) { best = change; since_best = 0; }
@@ -527,9 +526,9 @@ DBuf solve_signs(const EnvImpl &ref, const std::vector<const double *> &cand, cu
     res = std::max(res, std::sqrt(std::max(0.0, 2.0 - 2.0 * ov)));
   }
   if (residual) *residual = res;
+  // pageable source: the call returns once hs is staged, so hs may go out of scope
   DBuf out(hs.size(), s);
   IPEPS_CUDA(cudaMemcpyAsync(out.p, hs.data(), hs.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  IPEPS_CUDA(stream_sync(s));
   return out;
 }
 

@@ -686,7 +686,6 @@ void t_svd(Tape &t, int M, int k, int *U, int *S, int *V) {
     check_launch("t_svd block");
     IPEPS_CUDA(cudaMemcpyAsync(t.vp(*S), Sb.p, k * sizeof(double), cudaMemcpyDeviceToDevice, t.s));
     if (t.record) push_trunc_svd_node(t, M, *U, *S, *V, N, k, int(kb), std::move(Ub), std::move(Sb), std::move(Vb));
-    else IPEPS_CUDA(stream_sync(t.s));
     return;
   }
   auto *nd = new SVDNode;

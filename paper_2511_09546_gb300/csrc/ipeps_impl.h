@@ -88,8 +88,10 @@ int ctmrg_run(EnvImpl &e, const double *A_dev, double tol, int maxit, Prec prec,
               cudaStream_t s);
 // Normalised corner spectra of the env into e.spectra (device).
 void corner_spectra(EnvImpl &e, cudaStream_t s);
-// Largest spectral change between two spectra buffers.
-double spectra_change(const double *a, const double *b, int nmat, int chi, cudaStream_t s);
+// Largest spectral change between two spectra buffers; with count_dev, the
+// device int is read into *count_host by the same host wait.
+double spectra_change(const double *a, const double *b, int nmat, int chi, cudaStream_t s,
+                      const int *count_dev = nullptr, int *count_host = nullptr);
 // Sign gauge: signs per tensor leg such that ref ~ sign . cand elementwise.
 // Returns device buffer of (8 * nsites) x 2 x chi signs (prev, next per tensor).
 DBuf solve_signs(const EnvImpl &ref, const std::vector<const double *> &cand, cudaStream_t s,

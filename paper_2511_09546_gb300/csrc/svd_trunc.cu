@@ -278,7 +278,7 @@ bool svd_subspace(const double *M, int64_t N, int chi, int k, double *cache, dou
     IPEPS_CUDA(cudaMemcpyAsync(cache, Vc.p, size_t(N) * k * sizeof(double), cudaMemcpyDeviceToDevice, s));
     IPEPS_CUDA(cudaMemcpyAsync(cache + N * k, Sc.p, size_t(k) * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
-  IPEPS_CUDA(stream_sync(s));
+  // stream-ordered frees; the host vectors were copied from before their calls returned
   dev_free(dflag, s);
   dev_free(dperm, s);
   if (iters) *iters = it;
