@@ -69,6 +69,8 @@ const char *shape_class(const char *base, int64_t M, int64_t N, int64_t K) {
 ProfScope::ProfScope(const char *name, cudaStream_t s, double flops, double bytes)
     : name_(name), s_(s), flops_(flops), bytes_(bytes) {
   if (!g_on) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s_, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;  // graph capture
   a_ = take_event();
   b_ = take_event();
   cudaEventRecord(a_, s_);
