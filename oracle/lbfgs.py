@@ -62,13 +62,22 @@ def hz_linesearch(phi, phi0, dphi0, c, p: HZParams = HZParams()):
         t2 = ((2.0 * p.delta - 1.0) * dphi0 >= da >= p.sigma * dphi0) and (fa <= fmax)
         return t1 or t2
 
+    repeats = [0]
+
     def ev(a):
         if a not in cache:
+            repeats[0] = 0
             if len(cache) > p.max_evals:
                 raise _Found(None)
             cache[a] = phi(a)
             if ok(a, cache[a][0], cache[a][1]):
                 raise _Found(a)
+        else:
+            # an interval shrunk to adjacent doubles keeps asking for its own
+            # ends: end the search as when the budget is spent
+            repeats[0] += 1
+            if repeats[0] > 50:
+                raise _Found(None)
         return cache[a][0], cache[a][1]
 
     def bisect(a, b):

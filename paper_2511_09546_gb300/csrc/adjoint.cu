@@ -105,123 +105,35 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   }
 
   // ---- vector-Jacobian products of F
-  auto vjp_on = [&](cudaStream_t st, const double *lam, double *out_env, double *out_A) {
+  auto vjp = [&](const double *lam, double *out_env, double *out_A) {
     tF.zero_grads();
     for (int n = 0; n < 8; ++n)
       for (int i = 0; i < ns; ++i) {
         int k = n * ns + i;
         IPEPS_CUDA(cudaMemcpyAsync(tF.grad(outs[k]), lam + e.offset(n, i / c.Ly, i % c.Ly),
-                                   tF.val(outs[k]).size() * sizeof(double), cudaMemcpyDeviceToDevice, st));
+                                   tF.val(outs[k]).size() * sizeof(double), cudaMemcpyDeviceToDevice, s));
       }
     tF.backward();
     if (out_env) {
-      fill(out_env, nenv, 0.0, st);
+      fill(out_env, nenv, 0.0, s);
       for (int n = 0; n < 8; ++n)
         for (int i = 0; i < ns; ++i) {
           double *g = tF.grad(in.env[n][i], false);
           if (g)
             IPEPS_CUDA(cudaMemcpyAsync(out_env + e.offset(n, i / c.Ly, i % c.Ly), g,
                                        tF.val(in.env[n][i]).size() * sizeof(double),
-                                       cudaMemcpyDeviceToDevice, st));
+                                       cudaMemcpyDeviceToDevice, s));
         }
     }
     if (out_A)
       for (int i = 0; i < ns; ++i) {
         double *g = tF.grad(in.A[0][i], false);
-        if (g) axpy(ta, 1.0, g, out_A + int64_t(i) * ta, st);
+        if (g) axpy(ta, 1.0, g, out_A + int64_t(i) * ta, s);
       }
-  };
-  auto vjp = [&](const double *lam, double *out_env, double *out_A) { vjp_on(s, lam, out_env, out_A); };
-  // The first matvec runs eagerly (it allocates every cotangent buffer and
-  // measures the SVD-adjoint CG); the second is captured once into a CUDA graph
-  // on a private stream, from fixed buffers X0 -> Y0, and every further matvec
-  // relaunches that graph: one launch instead of thousands of kernel launches
-  // and host waits.  IPEPS_ADJ_GRAPH=0 keeps every matvec eager.
-  static const bool use_graph = [] {
-    const char *v = std::getenv("IPEPS_ADJ_GRAPH");
-    return !(v && v[0] == '0');
-  }();
-  struct Graph {
-    cudaStream_t cs = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    cudaEvent_t e1 = nullptr, e2 = nullptr;
-    size_t kernels = 0;
-    bool tried = false;
-    ~Graph() {
-      if (exec) {
-        cudaGraphExecDestroy(exec);
-        int dev = 0;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGraphMemTrim(dev);  // return its temporaries
-      }
-      if (e1) cudaEventDestroy(e1);
-      if (e2) cudaEventDestroy(e2);
-      if (cs) {
-        cudaStreamSynchronize(cs);
-        cudaStreamDestroy(cs);
-      }
-    }
-  } gr;
-  DBuf X0, Y0;
-  int eager_mv = 0;
-  auto capture = [&]() {
-    gr.tried = true;
-    X0 = DBuf(size_t(nenv), s);
-    Y0 = DBuf(size_t(nenv), s);
-    IPEPS_CUDA(cudaStreamCreateWithFlags(&gr.cs, cudaStreamNonBlocking));
-    IPEPS_CUDA(cudaEventCreateWithFlags(&gr.e1, cudaEventDisableTiming));
-    IPEPS_CUDA(cudaEventCreateWithFlags(&gr.e2, cudaEventDisableTiming));
-    IPEPS_CUDA(cudaEventRecord(gr.e1, s));
-    IPEPS_CUDA(cudaStreamWaitEvent(gr.cs, gr.e1, 0));
-    const cudaStream_t keep = tF.s;
-    const uint64_t launches = launch_counter();
-    cudaGraph_t g = nullptr;
-    tF.s = gr.cs;
-    try {
-      IPEPS_CUDA(cudaStreamBeginCapture(gr.cs, cudaStreamCaptureModeThreadLocal));
-      try {
-        vjp_on(gr.cs, X0.p, Y0.p, nullptr);
-        axpby(nenv, 1.0, X0.p, -1.0, Y0.p, gr.cs);  // Y0 = X0 - J^T X0
-      } catch (...) {
-        cudaStreamEndCapture(gr.cs, &g);
-        throw;
-      }
-      IPEPS_CUDA(cudaStreamEndCapture(gr.cs, &g));
-      IPEPS_CUDA(cudaGraphInstantiate(&gr.exec, g, 0));
-      size_t nn = 0;
-      IPEPS_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
-      std::vector<cudaGraphNode_t> nodes(nn);
-      IPEPS_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
-      for (auto nd : nodes) {
-        cudaGraphNodeType ty;
-        IPEPS_CUDA(cudaGraphNodeGetType(nd, &ty));
-        if (ty == cudaGraphNodeTypeKernel) ++gr.kernels;
-      }
-    } catch (const std::exception &ex) {
-      if (gr.exec) cudaGraphExecDestroy(gr.exec);
-      gr.exec = nullptr;
-      cudaGetLastError();
-      if (std::getenv("IPEPS_DEBUG")) std::fprintf(stderr, "[ipeps] adjoint graph capture failed: %s\n", ex.what());
-    }
-    if (g) cudaGraphDestroy(g);
-    tF.s = keep;
-    launch_counter() = launches;  // the captured launches did not run
   };
   MatVec mv = [&](const double *x, double *y) {
-    if (use_graph && eager_mv >= 1 && !gr.tried) capture();
-    if (gr.exec) {
-      IPEPS_CUDA(cudaMemcpyAsync(X0.p, x, nenv * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      IPEPS_CUDA(cudaEventRecord(gr.e1, s));
-      IPEPS_CUDA(cudaStreamWaitEvent(gr.cs, gr.e1, 0));
-      IPEPS_CUDA(cudaGraphLaunch(gr.exec, gr.cs));
-      count_launch(gr.kernels);
-      IPEPS_CUDA(cudaEventRecord(gr.e2, gr.cs));
-      IPEPS_CUDA(cudaStreamWaitEvent(s, gr.e2, 0));
-      IPEPS_CUDA(cudaMemcpyAsync(y, Y0.p, nenv * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      return;
-    }
     vjp(x, y, nullptr);
     axpby(nenv, 1.0, x, -1.0, y, s);  // y = x - J^T x
-    ++eager_mv;
   };
   DBuf lam(size_t(nenv), s);
   int nmv = 0;
@@ -231,8 +143,8 @@ double energy_grad(const Cell &c, const double *A_dev, EnvImpl &e, const HamImpl
   double rel = gmres_dev(nenv, mv, ebar.p, lam.p, kry, rst, 1e-12, s, &nmv);
   lap("adjoint GMRES");
   if (dbg)
-    std::fprintf(stderr, "[ipeps] adjoint: %d matvecs, residual %.2e, fixed-point residual %.2e, cg %d, graph %s\n",
-                 nmv, rel, fpres, tF.svd_iters, gr.exec ? "yes" : "no");
+    std::fprintf(stderr, "[ipeps] adjoint: %d matvecs, residual %.2e, fixed-point residual %.2e, cg %d\n", nmv,
+                 rel, fpres, tF.svd_iters);
   vjp(lam.p, nullptr, grad);
   IPEPS_CUDA(stream_sync(s));
   if (adj_resid) *adj_resid = rel;

@@ -262,9 +262,16 @@ bool LbfgsRun::step(ipeps_iter_info *out) {
   vals[0.0] = {phi0, dphi0};
   double found = -1.0;
   struct Stop {};
+  int repeats = 0;  // consecutive requests of points already evaluated
   auto ev = [&](double a) -> std::pair<double, double> {
     auto it = vals.find(a);
-    if (it != vals.end()) return it->second;
+    if (it != vals.end()) {
+      // an interval shrunk to adjacent doubles keeps asking for its own ends:
+      // end the search with the best point, as when the budget is spent
+      if (++repeats > 50) throw Stop{};
+      return it->second;
+    }
+    repeats = 0;
     if (int(vals.size()) > max_evals) throw Stop{};
     auto p = std::make_unique<Point>();
     p->x = DBuf(size_t(n), s);

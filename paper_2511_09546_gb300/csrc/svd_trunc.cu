@@ -380,19 +380,11 @@ void col_axpy(int64_t rows, int n, double sgn, const double *f, const double *X,
   count_launch();
 }
 
-// CG step length for column i: rr_i / pk_i, and 0 once the column has converged
-// (rr_i <= (1e-12)^2 bb_i) or the curvature is not positive
-__global__ void cg_alpha_kernel(const double *rr, const double *pk, const double *bb, int n, double *out) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (rr[i] > 1e-24 * bb[i] && pk[i] > 0.0 && rr[i] > 0.0) ? rr[i] / pk[i] : 0.0;
-}
-
 struct TruncSVDNode : Node {
   int M, U, S, V;
   int64_t N;
   int chi, kb;
   DBuf Uk, Sk, Vk;  // row-major N x kb, kb
-  int eager_iters = 0;  // most CG steps an uncaptured replay of this node took
   void backward(Tape &t) override {
     double *gU = t.grad(U, false), *gS = t.grad(S, false), *gV = t.grad(V, false);
     if (!gU && !gS && !gV) return;
@@ -472,32 +464,6 @@ struct TruncSVDNode : Node {
     IPEPS_CUDA(cudaMemcpyAsync(P.p, R.p, 2 * n * c * sizeof(double), cudaMemcpyDeviceToDevice, s));
     coldot(2 * n, c, G.p, G.p, bb.p, s);
     coldot(2 * n, c, R.p, R.p, rr.p, s);
-    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-    IPEPS_CUDA(cudaStreamIsCapturing(s, &cap));
-    if (cap != cudaStreamCaptureStatusNone) {
-      // inside a CUDA graph (the adjoint's replay): no host checks; twice the
-      // steps the uncaptured replays needed, converged columns frozen on the
-      // device (a step of length 0)
-      const int iters = std::min(100, 2 * std::max(eager_iters, 4) + 2);
-      for (int it = 0; it < iters; ++it) {
-        K(P.p, KP.p);
-        coldot(2 * n, c, P.p, KP.p, pk.p, s);
-        cg_alpha_kernel<<<(c + 127) / 128, 128, 0, s>>>(rr.p, pk.p, bb.p, c, al.p);
-        count_launch();
-        col_axpy(2 * n, c, 1.0, al.p, P.p, X.p, s);
-        col_axpy(2 * n, c, -1.0, al.p, KP.p, R.p, s);
-        coldot(2 * n, c, R.p, R.p, rn.p, s);
-        ratio_kernel<<<(c + 127) / 128, 128, 0, s>>>(rn.p, rr.p, c, al.p);  // beta
-        count_launch();
-        col_xpby_kernel<<<512, 256, 0, s>>>(2 * n, c, al.p, R.p, P.p);
-        count_launch();
-        std::swap(rr, rn);
-      }
-      check_launch("trunc_svd_bwd (graph)");
-      gemm_f64(false, true, n, n, c, 1.0, XU, c, Vk.p, kb, 1.0, gM, n, s);
-      gemm_f64(false, true, n, n, c, 1.0, Uk.p, kb, XV, c, 1.0, gM, n, s);
-      return;
-    }
     std::vector<double> hb(c);
     IPEPS_CUDA(cudaMemcpyAsync(hb.data(), bb.p, c * sizeof(double), cudaMemcpyDeviceToHost, s));
     // Residuals come back through two pinned slots, one iteration late: the
@@ -536,7 +502,6 @@ struct TruncSVDNode : Node {
         if (hb[i] > 0.0) worst = std::max(worst, std::sqrt(hr[i] / hb[i]));
       t.svd_iters += 1;
       hist.push_back(worst);
-      eager_iters = std::max(eager_iters, it + 1);
       if (worst <= 1e-12) break;
       if (hist.size() > 4 && worst > 0.5 * hist[hist.size() - 4]) break;
     }
