@@ -194,6 +194,17 @@ struct ipeps_server_s {
       tuning[j.cls] = true;
     }
     double best_thr = ipeps::oz_threshold(), best_ms = INFINITY;
+    // the class always gets a crossover, also when a timing run fails
+    struct Publish {
+      ipeps_server_s &srv;
+      Job &j;
+      double &thr;
+      ~Publish() {
+        std::lock_guard<std::mutex> lk(srv.mu);
+        srv.tuned[j.cls] = thr;
+        srv.cv.notify_all();
+      }
+    } publish{*this, j, best_thr};
     if (ipeps::Prec(j.o.prec) == ipeps::Prec::FP64_TC || ipeps::Prec(j.o.prec) == ipeps::Prec::BF16X3) {
       ipeps::EnvImpl e;
       e.cell = j.c;
@@ -217,9 +228,6 @@ struct ipeps_server_s {
       }
     }
     ipeps::oz_threshold() = best_thr;
-    std::lock_guard<std::mutex> lk(mu);
-    tuned[j.cls] = best_thr;
-    cv.notify_all();
   }
 
   void release(Job &j) {

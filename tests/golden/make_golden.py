@@ -51,11 +51,18 @@ def rangefinder():
 
 
 def lbfgs():
-    """Oracle L-BFGS iterates at D=2, chi=16 from the seeded start of the
-    survey's first configuration: 5 plain iterations, 3 preconditioned."""
-    w = inputs.WORKLOADS["heis_d2_chi16"]
+    """Oracle L-BFGS iterates at D=2, chi=16: 5 plain iterations from the seeded
+    Neel-like start (the D=1 Neel state embedded in D=2 plus 1e-2 noise) and 3
+    preconditioned iterations from the seeded random start of the survey's first
+    configuration.  (From the random start the plain method's line searches run
+    their whole 40-evaluation budget at every iteration; from the Neel-like start
+    the preconditioned method's do from its second iteration on, because the
+    near-product state's local metric is nearly singular and delta = |g|^2 is
+    tiny: both too long for the GPU suite.)"""
     out = {}
-    for name, pre, iters in (("plain", False, 5), ("preconditioned", True, 3)):
+    for name, pre, iters, wname in (("plain", False, 5, "heis_d2_chi16_neel"),
+                                    ("preconditioned", True, 3, "heis_d2_chi16")):
+        w = inputs.WORKLOADS[wname]
         t0 = time.time()
         cell = w["gen"]()
 
@@ -64,9 +71,10 @@ def lbfgs():
 
         _, _, log = OO.optimize(cell, OM.heisenberg(True), w["chi"], precond=pre, maxiter=iters, tol=1e-11,
                                 ctm_maxit=150, callback=cb)
-        out[name] = {"iterations": iters, "log": [{k: (float(v) if k != "k" else int(v)) for k, v in r.items()}
-                                                  for r in log], "seconds": time.time() - t0}
-    _write("lbfgs_heis_d2_chi16.json", {"workload": "heis_d2_chi16", "ctm_tol": 1e-11, "ctm_maxit": 150, **out})
+        out[name] = {"workload": wname, "iterations": iters,
+                     "log": [{k: (float(v) if k != "k" else int(v)) for k, v in r.items()} for r in log],
+                     "seconds": time.time() - t0}
+    _write("lbfgs_heis_d2_chi16.json", {"ctm_tol": 1e-11, "ctm_maxit": 150, **out})
 
 
 if __name__ == "__main__":
