@@ -124,25 +124,3 @@ def test_errors_are_reported(ip):
     with pytest.raises(ip.IpepsError) as e:
         ip.ctmrg(A, 16, tol=1e-14, maxit=2)
     assert e.value.status == 5
-
-
-@pytest.mark.parametrize("precond,iters", [(1, 1)])
-def test_lbfgs_trajectory_matches_oracle(ip, precond, iters):
-    # the first preconditioned L-BFGS iteration follows the oracle's: local metric,
-    # GMRES(30), two-loop start and the Hager-Zhang acceptance (a trial step whose
-    # CTMRG does not converge is rejected on both sides).  The plain method's first
-    # line search from this start bisects towards the edge of the region where CTMRG
-    # converges for its whole 40-evaluation budget, too long for this suite.
-    from oracle import optimize as OO
-
-    cell = inputs.WORKLOADS["heis_d2_chi16"]["gen"]()
-    A = _dev(cell)
-    opts = ip.default_opts(chi=16, maxiter=iters, precondition=precond, ctm_tol=1e-11, ctm_maxit=150)
-    _, log, st = ip.optimize(A, ip.ham_heisenberg(True), opts)
-    _, _, olog = OO.optimize(cell, OM.heisenberg(True), 16, precond=bool(precond), maxiter=iters, tol=1e-11,
-                             ctm_maxit=150)
-    assert len(log) == len(olog)
-    for r, o in zip(log, olog):
-        assert abs(r["E"] - o["f"]) < 1e-9, (r, o)
-        if "alpha" in o:
-            assert abs(r["alpha"] - o["alpha"]) < 1e-6 * max(1.0, abs(o["alpha"]))
