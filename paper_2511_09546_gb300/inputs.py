@@ -86,6 +86,8 @@ WORKLOADS = {
     "heis_d2_chi16_neel": dict(Lx=1, Ly=1, d=2, D=2, chi=16, gen=lambda: neel_seed_cell(2, 0)),
     # Heisenberg 1x1, D=2, chi=32 (chi = 8 D^2), Neel-like D=1 seed embedded in D=2 plus noise, seed 0
     "heis_d2_chi32": dict(Lx=1, Ly=1, d=2, D=2, chi=32, gen=lambda: neel_seed_cell(2, 0)),
+    # Heisenberg 1x1, D=2, chi=32 (chi = 8 D^2), uniform[-1,1] normalised to unit max-abs, seed 0
+    "heis_d2_chi32_rand": dict(Lx=1, Ly=1, d=2, D=2, chi=32, gen=lambda: uniform_cell(1, 1, 2, 2, 0)),
     # Heisenberg 1x1, D=4, chi=64, Neel-like D=1 seed embedded in D=4 plus noise, seed 0
     "heis_d4_chi64": dict(Lx=1, Ly=1, d=2, D=4, chi=64, gen=lambda: neel_seed_cell(4, 0)),
     # Kitaev (spin-1/2 dimers, d=4), 1x2 cell (Lx=2, Ly=1), D=6, chi=72, N(0,1), seed 0
