@@ -1,5 +1,5 @@
-"""iPEPS energy minimisation with plain or local-metric preconditioned
-L-BFGS (oracle, test infrastructure).
+"""iPEPS energy minimisation with plain, local-metric or mean-field (chi = 1)
+preconditioned L-BFGS (oracle, test infrastructure).
 
 Sec. IV.A: the objective is E(A) of Sec. III.A with its gradient; the
 preconditioner is the local metric of Eq. (equ:local_metric), regularised by
@@ -16,6 +16,7 @@ import torch
 from . import ctmrg as C
 from .gradient import energy_and_gradient
 from .lbfgs import lbfgs
+from .bp import bp_precondition
 from .metric import local_metric, precondition
 
 
@@ -29,7 +30,9 @@ def _unpack(x, Lx, Ly, shape):
 
 
 def optimize(cell, ham, chi, *, precond=True, maxiter=10, tol=1e-12, krylov=30, restarts=1,
-             m=200, callback=None, stop=None, ctm_maxit=300):
+             m=200, callback=None, stop=None, ctm_maxit=300, bp_tol=1e-12, bp_maxit=1000):
+    """precond: False (plain L-BFGS), True or "local" (local metric), "bp"
+    (the chi = 1 mean-field metric of Sec. III.B, oracle/bp.py)."""
     Lx, Ly = len(cell), len(cell[0])
     shape = cell[0][0].shape
 
@@ -41,6 +44,11 @@ def optimize(cell, ham, chi, *, precond=True, maxiter=10, tol=1e-12, krylov=30, 
         if not info["converged"]:
             return np.inf, None, st
         return E, _pack(g), {"env": info["env"], "cell": c}
+
+    def pc_bp(st, v, delta):
+        vv = _unpack(v, Lx, Ly, shape)
+        out, _, _ = bp_precondition(st["cell"], vv, delta, tol=bp_tol, maxit=bp_maxit)
+        return np.concatenate([out[x][y].ravel() for x in range(Lx) for y in range(Ly)])
 
     def pc(st, v, delta):
         c, env = st["cell"], st["env"]
@@ -54,6 +62,7 @@ def optimize(cell, ham, chi, *, precond=True, maxiter=10, tol=1e-12, krylov=30, 
                 out.append(px.ravel())
         return np.concatenate(out)
 
-    x, f, g, log = lbfgs(fg, _pack(cell), precond=pc if precond else None, m=m, maxiter=maxiter,
+    pcf = pc_bp if precond == "bp" else (pc if precond else None)
+    x, f, g, log = lbfgs(fg, _pack(cell), precond=pcf, m=m, maxiter=maxiter,
                          callback=callback, stop=stop)
     return _unpack(x, Lx, Ly, shape), f, log
