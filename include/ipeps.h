@@ -179,13 +179,37 @@ ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, i
                                 const double *g_dev, double delta, int krylov, int restarts,
                                 double *out_dev, double *resid_out, ipeps_stream_t stream);
 
+/* Mean-field preconditioned gradient (Sec. III.B: the local metric with the
+ * environment's bond dimension set to 1, the environment belief propagation
+ * gives; App. A).  Messages: one real D x D matrix m[ket, bra] per bond and
+ * direction; site s sends through leg lam the contraction of A_s and A_s
+ * (physical legs joined) with the messages arriving on its other three legs,
+ * symmetrised and divided by its trace; sweeps update all messages from the
+ * previous sweep's, from identity / D, until no entry changes by more than
+ * bp_tol or bp_maxit sweeps ran.  The message arriving on leg u of site (x, y)
+ * is the one (x, y-1) sends down (y grows downwards), l: (x-1, y) sends
+ * right, d: (x, y+1) sends up, r: (x+1, y) sends left.  The metric of a site is
+ * N = 1_d (x) c m_u (x) m_l (x) m_d (x) m_r, c such that <A|N|A> = 1, and
+ * out = (N + delta I)^-1 g is applied exactly in the eigenbases of the four
+ * messages.  No environment is needed.  A_dev, g_dev, out_dev: device, layout
+ * of A (out_dev aliases neither); delta < 0 selects delta = max(|g|^2, 1e-12)
+ * as in ipeps_precondition.  D <= 32.  sweeps_out / change_out (host, may be
+ * NULL): sweeps run and the last largest change; reaching bp_maxit is not an
+ * error (the last messages are used).  IPEPS_ERR_NONFINITE if a message
+ * loses its positive trace. */
+ipeps_status ipeps_precondition_bp(const ipeps_shape *shape, const double *A_dev, const double *g_dev,
+                                   double delta, double bp_tol, int bp_maxit, double *out_dev, int *sweeps_out,
+                                   double *change_out, ipeps_stream_t stream);
+
 /* ----------------------------------------------------------------- S13 */
 typedef struct {
   int chi;              /* environment bond dimension */
   double ctm_tol;       /* CTMRG corner-spectrum tolerance */
   int ctm_maxit;        /* CTMRG iteration limit per evaluation */
   ipeps_prec prec;      /* contraction arithmetic */
-  int precondition;     /* 0: plain L-BFGS, 1: local-metric preconditioned */
+  int precondition;     /* 0: plain L-BFGS, 1: local-metric preconditioned,
+                           2: mean-field (chi = 1) metric, ipeps_precondition_bp
+                              with bp_tol 1e-12, bp_maxit 1000 (D <= 32) */
   int krylov, restarts; /* GMRES (30, 1 in Sec. III.C) */
   int delta_rule;       /* 0: delta = |g|^2, 1: delta = |E_k - E_{k-1}| (Sec. III.B) */
   int history;          /* L-BFGS history m (200 in Sec. IV.A) */

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libipeps.so")
 SOURCES = ["kernels.cu", "gemm_f64.cu", "gemm_tc.cu", "gemm_oz.cu", "svd.cu", "svd_trunc.cu", "engine.cu", "ctmrg.cu", "energy.cu",
-           "precond.cu", "adjoint.cu", "optimize.cu", "profile.cu", "capi.cu", "serve.cu"]
+           "precond.cu", "bp.cu", "adjoint.cu", "optimize.cu", "profile.cu", "capi.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

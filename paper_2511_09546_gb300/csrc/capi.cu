@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/ipeps.h"
+#include "bp.h"
 #include "common.h"
 #include "ipeps_impl.h"
 #include "kernels.h"
@@ -388,6 +389,39 @@ ipeps_status ipeps_precondition(const ipeps_shape *shape, const double *A_dev, i
   });
 }
 
+ipeps_status ipeps_precondition_bp(const ipeps_shape *shape, const double *A_dev, const double *g_dev,
+                                   double delta, double bp_tol, int bp_maxit, double *out_dev, int *sweeps_out,
+                                   double *change_out, ipeps_stream_t stream) {
+  return guarded([&]() {
+    ipeps::Cell c = cell_of(shape);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    IPEPS_REQUIRE(A_dev && g_dev && out_dev, "precondition_bp: NULL argument");
+    IPEPS_REQUIRE(c.D <= 32, "precondition_bp: bond dimension above 32");
+    IPEPS_REQUIRE(std::isfinite(delta), "precondition_bp: delta must be finite");
+    IPEPS_REQUIRE(bp_tol >= 0.0 && bp_maxit >= 1, "precondition_bp: bad sweep limits");
+    IPEPS_REQUIRE(out_dev != g_dev && out_dev != A_dev, "precondition_bp: out_dev must not alias A_dev or g_dev");
+    const int64_t n = int64_t(c.nsites()) * c.tsize();
+    check_finite(A_dev, n, s, "A");
+    check_finite(g_dev, n, s, "g");
+    if (delta < 0.0) {
+      // the |g|^2 rule of Sec. III.B, floored at 1e-12
+      ipeps::DBuf nr(1, s);
+      ipeps::nrm2(n, g_dev, nr.p, s);
+      double h = 0.0;
+      IPEPS_CUDA(cudaMemcpyAsync(&h, nr.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+      IPEPS_CUDA(cudaStreamSynchronize(s));
+      delta = std::max(h * h, 1e-12);
+    }
+    ipeps::BpMetric m;
+    ipeps::bp_metric(c, A_dev, bp_tol, bp_maxit, m, s);
+    ipeps::bp_apply(m, g_dev, delta, out_dev, s);
+    IPEPS_CUDA(cudaStreamSynchronize(s));
+    if (sweeps_out) *sweeps_out = m.sweeps;
+    if (change_out) *change_out = m.change;
+    return IPEPS_OK;
+  });
+}
+
 ipeps_status ipeps_gemm(ipeps_prec prec, int ta, int tb, int64_t M, int64_t N, int64_t K, double alpha,
                         const double *A, int64_t lda, const double *B, int64_t ldb, double beta, double *C,
                         int64_t ldc, ipeps_stream_t stream) {
@@ -451,7 +485,8 @@ ipeps_status ipeps_optimize(const ipeps_shape *shape, double *A_dev, ipeps_ham h
     IPEPS_REQUIRE(A_dev && ham && opts, "optimize: NULL argument");
     IPEPS_REQUIRE(opts->chi >= 1 && opts->ctm_maxit >= 1 && opts->history >= 0 && opts->maxiter >= 0 &&
                       opts->krylov >= 1 && opts->restarts >= 1 && opts->prec >= IPEPS_FP64 &&
-                      opts->prec <= IPEPS_BF16X3,
+                      opts->prec <= IPEPS_BF16X3 && opts->precondition >= 0 && opts->precondition <= 2 &&
+                      (opts->precondition != 2 || c.D <= 32),
                   "optimize: bad options");
     IPEPS_REQUIRE(ham->impl.d == c.d, "optimize: Hamiltonian has a different d");
     check_finite(A_dev, int64_t(c.nsites()) * c.tsize(), s, "A");

@@ -1,6 +1,8 @@
 // Plain and preconditioned L-BFGS with the Hager-Zhang line search (Sec. II:
 // the preconditioned gradient P^-1 g inside a quasi-Newton method; Sec. IV.A:
 // L-BFGS with m = 200 and the Hager-Zhang line search; Sec. III.B: delta).
+// P is the local metric (precondition = 1, precond.cu) or the mean-field
+// chi = 1 metric (precondition = 2, bp.cu).
 //
 // Host control, device vectors: the history pairs (s, y) live in HBM, every
 // inner product is a device reduction read back as one scalar, and each
@@ -24,6 +26,7 @@
 #include <map>
 #include <vector>
 
+#include "bp.h"
 #include "common.h"
 #include "ipeps_impl.h"
 #include "kernels.h"
@@ -38,6 +41,7 @@ struct Point {
   EnvImpl env;
   int ctm_iters = 0;
   bool ok = false;
+  std::unique_ptr<BpMetric> bp;  // mean-field metric of x, built on first use
 };
 
 double ddot(int64_t n, const double *a, const double *b, cudaStream_t s) {
@@ -109,7 +113,16 @@ struct Driver {
     if (!p.ok) p.f = INFINITY;
   }
 
-  void precond(const Point &p, const double *v, double delta, double *out) {
+  void precond(Point &p, const double *v, double delta, double *out) {
+    if (o.precondition == 2) {
+      // the mean-field metric depends on the tensor only: one build per point
+      if (!p.bp) {
+        p.bp = std::make_unique<BpMetric>();
+        bp_metric(c, p.x.p, kBpTol, kBpMaxit, *p.bp, s);
+      }
+      bp_apply(*p.bp, v, delta, out, s);
+      return;
+    }
     precondition_all(p.env, p.x.p, v, delta, o.krylov, o.restarts, out, s);
   }
 };

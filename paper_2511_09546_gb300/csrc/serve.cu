@@ -367,7 +367,8 @@ ipeps_status ipeps_server_submit(ipeps_server srv, const ipeps_job_desc *desc, u
                   "server_submit: bad shape");
     const ipeps_opts &o = desc->opts;
     IPEPS_REQUIRE(o.chi >= 1 && o.ctm_maxit >= 1 && o.history >= 0 && o.maxiter >= 0 && o.krylov >= 1 &&
-                      o.restarts >= 1 && o.prec >= IPEPS_FP64 && o.prec <= IPEPS_BF16X3,
+                      o.restarts >= 1 && o.prec >= IPEPS_FP64 && o.prec <= IPEPS_BF16X3 &&
+                      o.precondition >= 0 && o.precondition <= 2 && (o.precondition != 2 || sh.D <= 32),
                   "server_submit: bad options");
     const ipeps::HamImpl &H = desc->ham->impl;
     IPEPS_REQUIRE(H.d == sh.d, "server_submit: Hamiltonian has a different d");

@@ -78,6 +78,7 @@ def lib():
         L.ipeps_energy.argtypes = [sp, vp, vp, vp, dp, vp]
         L.ipeps_energy_grad.argtypes = [sp, vp, vp, vp, dp, vp, vp]
         L.ipeps_precondition.argtypes = [sp, vp, vp, vp, d, i, i, vp, dp, vp]
+        L.ipeps_precondition_bp.argtypes = [sp, vp, vp, d, d, i, vp, C.POINTER(i), dp, vp]
         L.ipeps_opts_default.argtypes = [C.POINTER(Opts)]
         i64 = C.c_int64
         L.ipeps_gemm.argtypes = [i, i, i, i64, i64, i64, d, vp, i64, vp, i64, d, vp, i64, vp]
@@ -240,6 +241,23 @@ def precondition(A, env, g, delta, krylov=30, restarts=1):
     _check(lib().ipeps_precondition(C.byref(shape), C.c_void_p(A.data_ptr()), env.h, C.c_void_p(g.data_ptr()),
                                     delta, krylov, restarts, C.c_void_p(out.data_ptr()), C.byref(res), _stream()))
     return out, res.value
+
+
+def precondition_bp(A, g, delta, tol=1e-12, maxit=1000):
+    """(N + delta I)^-1 g with N the mean-field (chi = 1) metric of every tensor;
+    needs no environment.  Returns (x, sweeps, last largest message change)."""
+    A = _dev(A)
+    g = _dev(g)
+    if g.shape != A.shape:
+        raise ValueError("precondition_bp: g must have the shape of A")
+    shape = _shape(A)
+    out = torch.empty_like(g)
+    sweeps = C.c_int()
+    change = C.c_double()
+    _check(lib().ipeps_precondition_bp(C.byref(shape), C.c_void_p(A.data_ptr()), C.c_void_p(g.data_ptr()),
+                                       delta, tol, maxit, C.c_void_p(out.data_ptr()), C.byref(sweeps),
+                                       C.byref(change), _stream()))
+    return out, sweeps.value, change.value
 
 
 def default_opts(**kw):

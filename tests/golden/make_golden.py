@@ -5,6 +5,7 @@ generators; nothing here calls the CUDA path.
 
   python tests/golden/make_golden.py rangefinder   # D=5, chi=44 truncated-SVD case
   python tests/golden/make_golden.py lbfgs         # plain (5) and preconditioned (3) L-BFGS iterations
+  python tests/golden/make_golden.py lbfgs_bp      # mean-field (chi = 1) preconditioned L-BFGS iteration
 """
 import json
 import os
@@ -77,5 +78,24 @@ def lbfgs():
     _write("lbfgs_heis_d2_chi16.json", {"ctm_tol": 1e-11, "ctm_maxit": 150, **out})
 
 
+def lbfgs_bp():
+    """The first oracle L-BFGS iteration with the mean-field (chi = 1) metric
+    preconditioner (Sec. III.B, App. A) from the seeded Neel-like D=2 start,
+    chi = 16.  (Its second line search runs the whole 40-evaluation budget.)"""
+    w = inputs.WORKLOADS["heis_d2_chi16_neel"]
+    t0 = time.time()
+
+    def cb(rec):
+        print("bp", rec, flush=True)
+
+    _, _, log = OO.optimize(w["gen"](), OM.heisenberg(True), w["chi"], precond="bp", maxiter=1, tol=1e-11,
+                            ctm_maxit=150, callback=cb)
+    _write("lbfgs_bp_heis_d2_chi16.json",
+           {"ctm_tol": 1e-11, "ctm_maxit": 150, "bp_tol": 1e-12, "bp_maxit": 1000,
+            "workload": "heis_d2_chi16_neel", "iterations": 1,
+            "log": [{k: (float(v) if k != "k" else int(v)) for k, v in r.items()} for r in log],
+            "seconds": time.time() - t0})
+
+
 if __name__ == "__main__":
-    {"rangefinder": rangefinder, "lbfgs": lbfgs}[sys.argv[1]]()
+    {"rangefinder": rangefinder, "lbfgs": lbfgs, "lbfgs_bp": lbfgs_bp}[sys.argv[1]]()

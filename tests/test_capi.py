@@ -24,7 +24,7 @@ def lib():
 
 def test_header_declares_the_hot_path():
     names = _declared()
-    for must in ("ipeps_ctmrg", "ipeps_energy_grad", "ipeps_precondition", "ipeps_optimize",
+    for must in ("ipeps_ctmrg", "ipeps_energy_grad", "ipeps_precondition", "ipeps_precondition_bp", "ipeps_optimize",
                  "ipeps_ham_create", "ipeps_env_destroy", "ipeps_last_error"):
         assert must in names
 
@@ -74,3 +74,31 @@ def test_job_footprint_host_logic(lib):
     assert 0 < a < b < c
     assert 3.0 < (b - (64 << 20)) / (a - (64 << 20)) < 4.5
     assert ipeps.job_footprint(0, 1, 2, 4, 64) == 0
+
+
+def test_precondition_bp_argument_checks_on_host(lib):
+    # the mean-field preconditioner rejects bad arguments before any device work
+    import ctypes as C
+
+    from paper_2511_09546_gb300 import ipeps
+
+    L = ipeps.lib()
+    sh = ipeps.Shape(1, 1, 2, 2)
+    out = C.c_void_p(16)
+    st = L.ipeps_precondition_bp(None, None, None, -1.0, 1e-12, 100, None, None, None, None)
+    assert st == 1 and b"shape" in L.ipeps_last_error()
+    st = L.ipeps_precondition_bp(C.byref(sh), None, None, -1.0, 1e-12, 100, out, None, None, None)
+    assert st == 1 and b"NULL" in L.ipeps_last_error()
+    big = ipeps.Shape(1, 1, 2, 33)
+    st = L.ipeps_precondition_bp(C.byref(big), C.c_void_p(8), C.c_void_p(16), -1.0, 1e-12, 100,
+                                 C.c_void_p(24), None, None, None)
+    assert st == 1 and b"above 32" in L.ipeps_last_error()
+    st = L.ipeps_precondition_bp(C.byref(sh), C.c_void_p(8), C.c_void_p(16), float("nan"), 1e-12, 100,
+                                 C.c_void_p(24), None, None, None)
+    assert st == 1 and b"finite" in L.ipeps_last_error()
+    st = L.ipeps_precondition_bp(C.byref(sh), C.c_void_p(8), C.c_void_p(16), 0.1, 1e-12, 0,
+                                 C.c_void_p(24), None, None, None)
+    assert st == 1 and b"sweep" in L.ipeps_last_error()
+    st = L.ipeps_precondition_bp(C.byref(sh), C.c_void_p(8), C.c_void_p(16), 0.1, 1e-12, 10,
+                                 C.c_void_p(16), None, None, None)
+    assert st == 1 and b"alias" in L.ipeps_last_error()
