@@ -345,8 +345,47 @@ def run_ours(args, rank, world, local):
         "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3),
                         "tflops": round(v["flops"] / max(1e-9, v["ms"] * 1e-3) / 1e12, 4)}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])},
+        "hbm_kernels": hbm_kernels(prof, _peaks().get("hbm_gbs", 6784.5)),
     }
+    rec["preconditioners_ms"] = precond_timings(ipeps, devA[W + K - 1], env, g)
     return rec
+
+
+def hbm_kernels(prof, hbm_peak):
+    """Achieved GB/s of the data-movement kernel classes (permutations, digit
+    packing) over the timed passes, against the measured copy bandwidth."""
+    out = {}
+    for k, v in prof.items():
+        if v["flops"] == 0 and v["bytes"] > 0 and v["ms"] > 0:
+            gbs = v["bytes"] / (v["ms"] * 1e-3) / 1e9
+            out[k] = {"launches": v["count"], "gb_per_launch": v["bytes"] / max(1, v["count"]) / 1e9,
+                      "achieved_gbs": gbs, "frac": gbs / hbm_peak if hbm_peak else None}
+    return out
+
+
+def precond_timings(ipeps, A, env, g, reps=3):
+    """Milliseconds per call of the two preconditioners at the last pass's
+    tensor (local metric + GMRES(30); mean-field metric), outside the timed
+    region; None where a call fails (reported, not fatal)."""
+    import torch
+
+    res = {}
+    for name, fn in (("local_metric_gmres30", lambda: ipeps.precondition(A, env, g, -1.0)),
+                     ("mean_field_bp", lambda: ipeps.precondition_bp(A, g, -1.0))):
+        try:
+            fn()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                r = fn()
+            torch.cuda.synchronize()
+            res[name] = 1e3 * (time.perf_counter() - t0) / reps
+            if name == "mean_field_bp":
+                res["mean_field_bp_sweeps"] = r[1]
+        except Exception as exc:  # noqa: BLE001 - reported in the JSON line
+            res[name] = None
+            res[name + "_error"] = str(exc)[:200]
+    return res
 
 
 # --------------------------------------------------------------- oracle side

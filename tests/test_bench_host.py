@@ -32,3 +32,23 @@ def test_perturbed_cells_are_seeded_and_close():
         assert (ca[0][0] == cb[0][0]).all()
         assert abs(ca[0][0] - c0[0][0]).max() <= 1e-3
     assert not (a[0][0][0] == a[1][0][0]).all()
+
+
+def test_hbm_kernel_table_uses_data_movement_classes_only():
+    prof = {"permute": {"count": 10, "ms": 2.0, "flops": 0.0, "bytes": 4e9},
+            "dgemm": {"count": 5, "ms": 1.0, "flops": 1e9, "bytes": 1e8},
+            "jacobi_pair": {"count": 3, "ms": 1.0, "flops": 0.0, "bytes": 0.0}}
+    t = bench.hbm_kernels(prof, 8000.0)
+    assert list(t) == ["permute"]
+    assert t["permute"]["achieved_gbs"] == pytest.approx(2000.0)
+    assert t["permute"]["frac"] == pytest.approx(0.25)
+    assert t["permute"]["gb_per_launch"] == pytest.approx(0.4)
+
+
+def test_roofline_picks_the_dominant_class():
+    prof = {"permute": {"count": 10, "ms": 2.0, "flops": 0.0, "bytes": 4e9},
+            "dgemm": {"count": 5, "ms": 6.0, "flops": 3e9, "bytes": 1e8}}
+    r = bench.roofline(prof, {"fp64_tflops": 1.0})
+    assert r["kernel"] == "dgemm" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(0.5) and r["frac"] == pytest.approx(0.5)
+    assert r["share"] == pytest.approx(0.75)
