@@ -25,9 +25,11 @@
  *     thread-local message from ipeps_last_error().  Inputs are FP64; the
  *     precision enum only selects the arithmetic of the bulk contractions.
  *   - No call launches a kernel that waits on another launch.
- *   - One device per process: the allocation pool and the 3xTF32 GEMM's
- *     error word and kernel attributes are set up on the device that is
- *     current at first use (run one process per GPU, as multi-GPU replicas do).
+ *   - Calls run on the calling thread's current CUDA device (device index
+ *     below 64).  The allocation pool setting, the tensor-core error word,
+ *     kernel attributes and SM counts are kept per device, so one process
+ *     may drive several devices from different threads; an ipeps_env or a
+ *     server belongs to the device that was current when it was created.
  */
 #ifndef IPEPS_H
 #define IPEPS_H

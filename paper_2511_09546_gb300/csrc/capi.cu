@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <set>
+#include <mutex>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -42,17 +45,51 @@ void check_launch(const char *what) {
   if (e != cudaSuccess) throw Error(IPEPS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-void *dev_alloc(size_t bytes, cudaStream_t s) {
-  static bool pool_ready = false;
-  if (!pool_ready) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaMemPool_t pool;
-    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-      uint64_t keep = UINT64_MAX;
-      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+int current_device() {
+  int d = 0;
+  IPEPS_CUDA(cudaGetDevice(&d));
+  IPEPS_REQUIRE(d >= 0 && d < kMaxDevices, "device index above the library's limit of 64");
+  return d;
+}
+
+int device_sm_count() {
+  static std::atomic<int> sms[kMaxDevices];  // zero-initialised
+  const int d = current_device();
+  int v = sms[d].load(std::memory_order_relaxed);
+  if (!v) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess || v <= 0) {
+      cudaGetLastError();
+      v = 152;
     }
-    pool_ready = true;
+    sms[d].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
+void once_per_device(const void *key, void (*f)(void *), void *arg) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(mu);
+  if (done.count({d, key})) return;
+  f(arg);
+  done.insert({d, key});
+}
+
+void *dev_alloc(size_t bytes, cudaStream_t s) {
+  // keep freed blocks in the current device's pool (its release threshold)
+  static std::atomic<bool> pool_ready[kMaxDevices];
+  const int dev = current_device();
+  if (!pool_ready[dev].load(std::memory_order_acquire)) {
+    once_per_device(&pool_ready, [dev]() {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t keep = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+      }
+      cudaGetLastError();
+    });
+    pool_ready[dev].store(true, std::memory_order_release);
   }
   void *p = nullptr;
   if (bytes == 0) bytes = 8;

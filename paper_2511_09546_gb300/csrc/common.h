@@ -41,6 +41,22 @@ void check_launch(const char *what);
 cudaError_t stream_sync(cudaStream_t s);
 uint64_t &sync_counter();
 
+// Per-device state.  The library keeps nothing per process that belongs to
+// one GPU: SM counts, kernel attributes, the memory-pool setting and the
+// tensor-core error word are looked up by the calling thread's current device
+// (indices below kMaxDevices), so one process may drive several devices.
+constexpr int kMaxDevices = 64;
+int current_device();
+// SM count of the current device (queried once per device)
+int device_sm_count();
+// runs f() once per (current device, key), e.g. a kernel's shared-memory
+// attribute; a throwing f() is retried on the next call
+void once_per_device(const void *key, void (*f)(void *), void *arg);
+template <class F>
+void once_per_device(const void *key, F &&f) {
+  once_per_device(key, [](void *a) { (*static_cast<F *>(a))(); }, static_cast<void *>(&f));
+}
+
 // Stream-ordered device allocations (the pool keeps freed blocks cached).
 void *dev_alloc(size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);

@@ -145,16 +145,7 @@ __global__ void splitk_reduce(const double *__restrict__ W, int S, int64_t M, in
   }
 }
 
-int num_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
+int num_sms() { return device_sm_count(); }
 }  // namespace
 
 Prec &fp64_policy() {

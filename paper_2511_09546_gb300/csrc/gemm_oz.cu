@@ -401,15 +401,16 @@ __global__ void oz_reduce(const double *__restrict__ W, int Z, int64_t M, int64_
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 oz_encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  // a driver entry point, the same for every device (thread-safe static
+  // initialisation; a throw leaves it for the next call)
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
       throw Error(IPEPS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
   return fn;
 }
 
@@ -426,16 +427,7 @@ CUtensorMap oz_map(const __nv_bfloat16 *P, int64_t rows_pad, int64_t cols, int b
   return m;
 }
 
-int oz_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
-  return sms;
-}
+int oz_sms() { return device_sm_count(); }
 
 }  // namespace
 
@@ -502,11 +494,9 @@ void oz_multiply(const OzPacked &a, const OzPacked &b, int64_t M, int64_t N, dou
     ProfScope prof(shape_class(names[S], M, N, K), s, 2.0 * M * N * K,
                    2.0 * S * (Mp + Np) * Kp + 8.0 * M * N * (beta == 0.0 ? 1 : 2));
     constexpr size_t smem = size_t(ostages<S, BN>()) * stage_bytes<S, BN>() + 1024;
-    static bool attr = false;
-    if (!attr) {
+    once_per_device(reinterpret_cast<const void *>(oz_gemm_kernel<S, BN>), []() {
       IPEPS_CUDA(cudaFuncSetAttribute(oz_gemm_kernel<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-      attr = true;
-    }
+    });
     dim3 grid(unsigned(Np / BN), unsigned(Mp / OBM), unsigned(Z));
     if (Z > 1)
       oz_gemm_kernel<S, BN><<<grid, othreads<BN>(), smem, s>>>(ma, mb, a.mx, b.mx, M, N, int(Kp), nk, kper, alpha,

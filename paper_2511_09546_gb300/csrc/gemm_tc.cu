@@ -36,6 +36,7 @@
 
 #include <cstdint>
 #include <cstdlib>
+#include <mutex>
 #include <string>
 
 #include "common.h"
@@ -279,15 +280,14 @@ __global__ void __launch_bounds__(256) split_pack_kernel(const double *__restric
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
     void *p = nullptr;
     cudaDriverEntryPointQueryResult q;
     cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
     if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
       throw Error(IPEPS_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
   return fn;
 }
 
@@ -309,11 +309,9 @@ void launch(const CUtensorMap &ma, const CUtensorMap &mb, int64_t M, int64_t N, 
             double alpha, double beta, double *C, int64_t ldc, int *err, cudaStream_t s) {
   constexpr size_t stage = size_t(BM + BN) * BKT * 4;
   constexpr size_t smem = (RING_BYTES / stage) * stage + 1024;
-  static bool attr = false;
-  if (!attr) {
+  once_per_device(reinterpret_cast<const void *>(tc_gemm_kernel<BN, COMP>), []() {
     IPEPS_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<BN, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
-    attr = true;
-  }
+  });
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(unsigned(Np / BN), unsigned((M + BM - 1) / BM));
   cfg.blockDim = dim3(threads<BN>());
@@ -389,16 +387,21 @@ void gemm_tf32x3(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
   dev_free(Bp, s);
 }
 
-// The error word of the tensor-core kernels: one device int per process,
+// The error word of the tensor-core kernels: one device int per device,
 // raised by a kernel whose bounded mbarrier wait expired.  Launches do not
 // synchronise; the C ABI reads the word once per call (tc_check_errors).
 int *tc_error_word() {
-  static int *w = nullptr;
-  if (!w) {
-    IPEPS_CUDA(cudaMalloc(&w, sizeof(int)));
-    IPEPS_CUDA(cudaMemset(w, 0, sizeof(int)));
+  static int *w[kMaxDevices] = {};
+  static std::mutex mu;
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(mu);
+  if (!w[d]) {
+    int *p = nullptr;
+    IPEPS_CUDA(cudaMalloc(&p, sizeof(int)));
+    IPEPS_CUDA(cudaMemset(p, 0, sizeof(int)));
+    w[d] = p;
   }
-  return w;
+  return w[d];
 }
 
 void tc_check_errors(cudaStream_t s) {

@@ -11,13 +11,7 @@ namespace ipeps {
 namespace {
 
 int grid_for(int64_t n, int threads = 256) {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-  }
+  const int sms = device_sm_count();
   int64_t want = (n + threads - 1) / threads;
   int64_t cap = int64_t(sms) * 8;
   if (want < 1) want = 1;
