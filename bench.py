@@ -543,6 +543,11 @@ def run_ctmrg(args):
            "tc_gemm": {"share": gm["ms"] / tot_ms, "launches": gm["count"],
                        "logical_tflops": gm["flops"] / max(1e-9, gm["ms"] * 1e-3) / 1e12,
                        "issued_frac_of_tf32_peak": 3 * gm["flops"] / max(1e-9, gm["ms"] * 1e-3) / 1e12 / tf32_peak},
+           "digit_gemm": {k: {"share": st[k]["ms"] / tot_ms, "launches": st[k]["count"],
+                              "logical_tflops": st[k]["flops"] / max(1e-9, st[k]["ms"] * 1e-3) / 1e12,
+                              "issued_frac_of_bf16_peak": prods * st[k]["flops"] / max(1e-9, st[k]["ms"] * 1e-3)
+                              / 1e12 / _peaks().get("bf16_tflops_sustained", 1705.9)}
+                          for k, prods in (("oz2_gemm", 3), ("oz8_gemm", 36)) if k in st},
            "peaks_live": peaks_live,
            "last_change": err, "device_bytes_after_warmup": int(free0 - free1),
            "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 2),
