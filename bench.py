@@ -38,8 +38,18 @@ PASS_SEED = 11       # seed of the perturbation sequence
 PASS_TOL = 1e-10     # CTMRG tolerance of a pass
 PASS_MAXIT = 200     # CTMRG iteration limit of a pass
 # DRAM bytes per launch of the dominant kernels from one ncu capture (see
-# profiles/); a kernel changed since its capture has no entry
+# profiles/); a kernel changed since its capture has no entry.  A profiler
+# class spans launches of many shapes, so a single captured launch does not
+# give the class's per-launch traffic: those captures are listed as samples
+# (one launch, its shape, its DRAM bytes and its own algorithmic bytes).
 NCU_TRAFFIC = {}
+NCU_SAMPLES = {
+    "dgemm": {"launch": "dgemm_kernel 64 x 1024 x 64, split K 4 (profiles/dgemm_heis_d4_chi64_ncu.md)",
+              "dram_bytes": 582400, "operand_bytes": 8 * (64 * 64 + 64 * 1024), "us": 25.2},
+    "jacobi_pair": {"launch": "jacobi_pair_kernel, N = 1024 cold-start SVD pair step "
+                              "(profiles/jacobi_pair_heis_d4_chi64_ncu.md)",
+                    "dram_bytes": 9243648, "us": 2482.0},
+}
 
 
 def metric_name(workload):
@@ -212,6 +222,8 @@ def roofline(prof, peaks_live):
     roof["frac"] = roof["achieved"] / roof["peak"] if roof["peak"] else None
     tr = NCU_TRAFFIC.get(dom)
     roof["traffic"] = tr["bytes_per_launch"] if tr else None
+    if dom in NCU_SAMPLES:
+        roof["ncu_sample"] = NCU_SAMPLES[dom]
     roof["algorithmic_bytes_per_launch"] = st["bytes"] / max(1, st["count"])
     roof["share"] = st["ms"] / max(1e-9, total)
     roof["launches"] = st["count"]
