@@ -19,14 +19,21 @@ namespace ipeps {
 namespace {
 constexpr int BM = 64, BN = 64, BK = 8;
 
+// C tile of TM x TN per CTA of 256 threads (16 x 16, each (TM/16) x (TN/16)
+// outputs), K staged in slices of BK through shared memory.  TM = TN = 64 in
+// general; 32 x 32 tiles quadruple the CTA count of small outputs, whose 64 x 64
+// tiles leave most SMs idle (the FP64 pipe of each occupied SM is the limit).
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M, int64_t N, int64_t K,
                                                     double alpha, const double *__restrict__ A,
                                                     int64_t lda, const double *__restrict__ B,
                                                     int64_t ldb, double beta, double *__restrict__ C,
                                                     int64_t ldc, int64_t sA, int64_t sB, int64_t sC,
                                                     int64_t kchunk) {
-  __shared__ double As[BK][BM + 1];
-  __shared__ double Bs[BK][BN + 1];
+  static_assert(TM % 16 == 0 && TN % 16 == 0 && TM <= 64 && TN <= 64, "dgemm tile");
+  constexpr int RM = TM / 16, RN = TN / 16;
+  __shared__ double As[BK][TM + 1];
+  __shared__ double Bs[BK][TN + 1];
   // batched: blockIdx.z selects the matrix; split-K (kchunk > 0): blockIdx.z
   // selects a K range and C is the slice's partial-sum buffer
   const int64_t bz = blockIdx.z;
@@ -41,20 +48,20 @@ __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M,
     C += bz * sC;
   }
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = int64_t(blockIdx.y) * BM, n0 = int64_t(blockIdx.x) * BN;
-  double acc[4][4] = {};
+  const int64_t m0 = int64_t(blockIdx.y) * TM, n0 = int64_t(blockIdx.x) * TN;
+  double acc[RM][RN] = {};
   for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int e = threadIdx.x; e < BM * BK; e += 256) {
+    for (int e = threadIdx.x; e < TM * BK; e += 256) {
       int mm, kk;
-      if (!ta) { mm = e / BK; kk = e % BK; } else { kk = e / BM; mm = e % BM; }
+      if (!ta) { mm = e / BK; kk = e % BK; } else { kk = e / TM; mm = e % TM; }
       int64_t gm = m0 + mm, gk = k0 + kk;
       double v = 0.0;
       if (gm < M && gk < kend) v = ta ? A[gk * lda + gm] : A[gm * lda + gk];
       As[kk][mm] = v;
     }
-    for (int e = threadIdx.x; e < BN * BK; e += 256) {
+    for (int e = threadIdx.x; e < TN * BK; e += 256) {
       int nn, kk;
-      if (!tb) { kk = e / BN; nn = e % BN; } else { nn = e / BK; kk = e % BK; }
+      if (!tb) { kk = e / TN; nn = e % TN; } else { nn = e / BK; kk = e % BK; }
       int64_t gn = n0 + nn, gk = k0 + kk;
       double v = 0.0;
       if (gn < N && gk < kend) v = tb ? B[gn * ldb + gk] : B[gk * ldb + gn];
@@ -63,24 +70,24 @@ __global__ void __launch_bounds__(256) dgemm_kernel(bool ta, bool tb, int64_t M,
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[RM], b[RN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < RM; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < RN; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < RN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RM; ++i) {
     int64_t gm = m0 + ty + 16 * i;
     if (gm >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RN; ++j) {
       int64_t gn = n0 + tx + 16 * j;
       if (gn >= N) continue;
       double v = alpha * acc[i][j];
@@ -189,7 +196,6 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
                 "gemm_f64: grid too large");
   ProfScope prof(shape_class("dgemm", M, N, K * batch), s, 2.0 * M * N * K * batch,
                  8.0 * batch * (M * K + K * N + M * N * (beta == 0.0 ? 1.0 : 2.0)));
-  const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch;
   const int sms = num_sms();
   if (batch == 1 && M * N <= 1024 && K >= 256) {
     const int64_t groups = (M * N + 7) / 8;
@@ -213,30 +219,62 @@ void gemm_f64(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, c
     check_launch("dgemm perout");
     return;
   }
-  if (batch == 1 && tiles < sms && K >= 32) {
-    // fewer output tiles than SMs: split K so that the tiles x slices CTAs fill
-    // the SMs in one wave (the FP64 pipe, ~2 DFMA per clock per SM, is the
-    // limit, so a CTA more than the SM count doubles the time), slices of at
-    // least 16, then reduce
-    int64_t S = std::min<int64_t>(sms / tiles, K / 16);
-    S = std::min<int64_t>(S, 512);
-    if (S >= 2) {
-      int64_t kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
-      S = (K + kchunk - 1) / kchunk;
-      double *W = static_cast<double *>(dev_alloc(size_t(S) * M * N * sizeof(double), s));
-      dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(S));
-      dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N, kchunk);
-      int64_t n = M * N;
-      int rg = int(std::min<int64_t>((n + 255) / 256, 4 * sms));
-      splitk_reduce<<<rg, 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
-      count_launch(2);
-      check_launch("dgemm splitk");
-      dev_free(W, s);
-      return;
-    }
+  // Tile plan.  The FP64 pipe of each occupied SM (~4 DFMA per ns) is the
+  // limit, so the time is about (CTA waves) x (DFMA per CTA) / rate, plus a
+  // reduce launch and its reads when K is split.  Candidates: 64 x 64 tiles,
+  // and 32 x 32 tiles when the 64 x 64 ones leave SMs idle; each with K
+  // unsplit, or split (batch 1) into the slices (of at least BK) that fill one
+  // wave.  The cheapest wins; ties keep the larger tile and fewer slices.
+  struct Plan { int tile; int64_t ctas, S, kchunk; double ns; };
+  auto cost = [&](int T, int64_t S, int64_t kchunk) {
+    Plan p{T, ((N + T - 1) / T) * ((M + T - 1) / T) * batch, S, kchunk, 0.0};
+    const int64_t kc = S > 1 ? kchunk : (K + BK - 1) / BK * BK;
+    p.ns = double((p.ctas * S + sms - 1) / sms) * T * T * kc / 4.0;
+    if (S > 1) p.ns += 2500.0 + double(S) * M * N * 8.0 / 5000.0;
+    return p;
+  };
+  auto split_of = [&](int T, Plan *out) {
+    const int64_t ctas = ((N + T - 1) / T) * ((M + T - 1) / T);
+    if (batch != 1 || ctas >= sms || K < 2 * BK) return false;
+    int64_t S = std::min<int64_t>({sms / ctas, K / BK, int64_t(512)});
+    if (S < 2) return false;
+    const int64_t kchunk = ((K + S - 1) / S + BK - 1) / BK * BK;
+    S = (K + kchunk - 1) / kchunk;
+    if (S < 2) return false;
+    *out = cost(T, S, kchunk);
+    return true;
+  };
+  constexpr int ST = 32;
+  Plan best = cost(BM, 1, 0), cand;
+  if (split_of(BM, &cand) && cand.ns < best.ns) best = cand;
+  if (((N + BN - 1) / BN) * ((M + BM - 1) / BM) * batch < sms) {
+    Plan small = cost(ST, 1, 0);
+    if (split_of(ST, &cand) && cand.ns < small.ns) small = cand;
+    if (small.ns < 0.95 * best.ns) best = small;
   }
-  dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(batch));
-  dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, 0);
+  IPEPS_REQUIRE((M + best.tile - 1) / best.tile <= 65535, "gemm_f64: grid too large");
+  const dim3 grd(unsigned((N + best.tile - 1) / best.tile), unsigned((M + best.tile - 1) / best.tile),
+                 unsigned(best.S > 1 ? best.S : batch));
+  if (best.S > 1) {
+    // split K: slice z writes its partial sums to W[z], a second kernel adds them in order
+    double *W = static_cast<double *>(dev_alloc(size_t(best.S) * M * N * sizeof(double), s));
+    if (best.tile == ST)
+      dgemm_kernel<ST, ST><<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N,
+                                                best.kchunk);
+    else
+      dgemm_kernel<BM, BN><<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N,
+                                                best.kchunk);
+    int rg = int(std::min<int64_t>((M * N + 255) / 256, 4 * sms));
+    splitk_reduce<<<rg, 256, 0, s>>>(W, int(best.S), M, N, beta, C, ldc);
+    count_launch(2);
+    check_launch("dgemm splitk");
+    dev_free(W, s);
+    return;
+  }
+  if (best.tile == ST)
+    dgemm_kernel<ST, ST><<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, 0);
+  else
+    dgemm_kernel<BM, BN><<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sA, sB, sC, 0);
   count_launch();
   check_launch("dgemm");
 }
@@ -321,7 +359,7 @@ void gemm_f64_noalloc(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double 
   S = (K + kchunk - 1) / kchunk;
   IPEPS_REQUIRE((M + BM - 1) / BM <= 65535, "gemm_noalloc: grid too large");
   dim3 grd(unsigned((N + BN - 1) / BN), unsigned((M + BM - 1) / BM), unsigned(S));
-  dgemm_kernel<<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N, kchunk);
+  dgemm_kernel<BM, BN><<<grd, 256, 0, s>>>(ta, tb, M, N, K, alpha, A, lda, B, ldb, 0.0, W, N, 0, 0, M * N, kchunk);
   splitk_reduce<<<int(std::min<int64_t>((M * N + 255) / 256, 4 * sms)), 256, 0, s>>>(W, int(S), M, N, beta, C, ldc);
   count_launch(2);
   check_launch("gemm_noalloc splitk");

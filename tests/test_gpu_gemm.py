@@ -10,6 +10,8 @@ SHAPES = [
     (40, 1, 278528), (7, 3, 5000),        # multi-dot split-K (tiny output, long K)
     (278528, 1, 40), (2, 256, 256),       # one thin side: per-output kernel
     (96, 96, 8192), (64, 128, 4096),      # few tiles, long K: tiled split-K
+    (64, 1024, 64), (1024, 64, 64),       # few 64 x 64 tiles: 32 x 32 tiles, split K
+    (40, 50, 12), (256, 256, 16),         # 32 x 32 tiles, K unsplit
     (1, 1, 1), (3, 5, 0),
 ]
 
