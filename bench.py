@@ -216,6 +216,9 @@ def roofline(prof, peaks_live):
         roof = {"kernel": dom, "bound": "alu", "achieved": st["flops"] / (st["ms"] * 1e-3) / 1e12,
                 "peak": peaks_live.get("fp64_tflops"), "unit": "TFLOP/s",
                 "peak_source": "measured: cuBLAS FP64 GEMM 4096^3 on this GPU (torch.matmul, best of 3)"}
+        if dom == "jacobi_pair":
+            roof["note"] = ("FP64 pipe bound (ncu sample); achieved counts only the 32 x 32 Gram products of "
+                            "each pair step (a lower bound: rotations and the inner eigensolve are excluded)")
     else:
         roof = {"kernel": dom, "bound": "hbm", "achieved": st["bytes"] / (st["ms"] * 1e-3) / 1e9,
                 "peak": peaks.get("hbm_gbs", 6784.5), "unit": "GB/s", "peak_source": "MEASURED_PEAKS.json hbm_gbs"}

@@ -243,8 +243,13 @@ int jacobi_svd_colmajor(double *G, int64_t m, int64_t n, double *V, cudaStream_t
   for (; sweep < max_sweeps; ++sweep) {
     IPEPS_CUDA(cudaMemsetAsync(off.p, 0, sizeof(double), s));
     dim3 grd(unsigned(nb / 2), unsigned(batch));
+    // algorithmic work counted per pair step: the 32 x 32 Gram matrices of all
+    // nb/2 pairs (2 m 32^2 flops each, done even for pairs that are already
+    // orthogonal); rotations and the inner eigensolve are not counted, so the
+    // rate derived from it is a lower bound
+    const double gram_flops = 2.0 * double(m) * PW * PW * (nb / 2) * batch;
     for (int step = 0; step < nb - 1; ++step) {
-      ProfScope prof("jacobi_pair", s, 0.0, 0.0);
+      ProfScope prof("jacobi_pair", s, gram_flops, 0.0);
       jacobi_pair_kernel<<<grd, 256, 0, s>>>(Gp.p, m, V ? Vp.p : nullptr, npad, nb, step, tol, off.p);
       count_launch();
     }
