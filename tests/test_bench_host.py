@@ -52,3 +52,12 @@ def test_roofline_picks_the_dominant_class():
     assert r["kernel"] == "dgemm" and r["bound"] == "alu"
     assert r["achieved"] == pytest.approx(0.5) and r["frac"] == pytest.approx(0.5)
     assert r["share"] == pytest.approx(0.75)
+
+
+def test_roofline_of_the_jacobi_class_is_an_fp64_rate_with_its_note():
+    prof = {"jacobi_pair": {"count": 100, "ms": 8.0, "flops": 4e9, "bytes": 0.0},
+            "dgemm": {"count": 5, "ms": 6.0, "flops": 3e9, "bytes": 1e8}}
+    r = bench.roofline(prof, {"fp64_tflops": 1.1})
+    assert r["kernel"] == "jacobi_pair" and r["bound"] == "alu"
+    assert r["achieved"] == pytest.approx(0.5) and r["frac"] == pytest.approx(0.5 / 1.1)
+    assert "lower bound" in r["note"] and r["ncu_sample"]["dram_bytes"] > 0
