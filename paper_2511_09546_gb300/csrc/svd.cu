@@ -110,12 +110,8 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(double *__restrict__ G
   __syncthreads();
   for (int sweep = 0; sweep < 12; ++sweep) {
     for (int round = 0; round < PW - 1; ++round) {
-      // the 16 rotations of this round: lanes 0..3 of warps 0..3, so that their
-      // FP64 divisions and square roots run on four SM sub-partitions at once
-      // (one warp would serialise them on the slow FP64 pipe)
-      if ((tid & 31) < 4 && (tid >> 5) < 4) {
-        const int pr = (tid >> 5) * 4 + (tid & 31);
-        int p = tourney(pr, round, PW), q = tourney(PW - 1 - pr, round, PW);
+      if (tid < PW / 2) {
+        int p = tourney(tid, round, PW), q = tourney(PW - 1 - tid, round, PW);
         if (p > q) { int t = p; p = q; q = t; }
         double a = Gm[p][p], b = Gm[q][q], g = Gm[p][q];
         double c = 1.0, s = 0.0;
@@ -125,7 +121,7 @@ __global__ void __launch_bounds__(256) jacobi_pair_kernel(double *__restrict__ G
           c = 1.0 / sqrt(1.0 + t * t);
           s = t * c;
         }
-        cs[pr] = c; sn[pr] = s; pp[pr] = p; qq[pr] = q;
+        cs[tid] = c; sn[tid] = s; pp[tid] = p; qq[tid] = q;
       }
       __syncthreads();
       // columns of Gm and Z
