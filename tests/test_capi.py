@@ -102,3 +102,19 @@ def test_precondition_bp_argument_checks_on_host(lib):
     st = L.ipeps_precondition_bp(C.byref(sh), C.c_void_p(8), C.c_void_p(16), 0.1, 1e-12, 10,
                                  C.c_void_p(16), None, None, None)
     assert st == 1 and b"alias" in L.ipeps_last_error()
+
+
+def test_optimize_rejects_unknown_preconditioner_on_host(lib):
+    # precondition must be 0 (plain), 1 (local metric) or 2 (mean-field, D <= 32);
+    # the options are checked before any device work
+    import ctypes as C
+
+    from paper_2511_09546_gb300 import ipeps
+
+    L = ipeps.lib()
+    h = ipeps.ham_heisenberg(True)
+    for pre, D in ((3, 2), (-1, 2), (2, 33)):
+        o = ipeps.default_opts(chi=8, precondition=pre)
+        sh = ipeps.Shape(1, 1, 2, D)
+        st = L.ipeps_optimize(C.byref(sh), C.c_void_p(8), h.h, C.byref(o), ipeps.ITER_CB(0), None, None)
+        assert st == 1 and b"bad options" in L.ipeps_last_error(), (pre, D)
