@@ -52,6 +52,19 @@ NCU_SAMPLES = {
 }
 
 
+def pass_config(workload):
+    """The workload part of the JSON line's config, the same for both arms."""
+    from paper_2511_09546_gb300 import inputs
+
+    w = inputs.WORKLOADS[workload]
+    desc = (": Heisenberg square lattice 1x1, d=2, D=4, chi=64, Neel-like D=1 seed in D=4 + 1e-2 noise (seed 0)"
+            if workload == "heis_d4_chi64" else "")
+    return {"workload": workload + desc,
+            "pass": f"tensor_k = start + {PASS_EPS:g} U[-1,1] (seed {PASS_SEED}); CTMRG to {PASS_TOL:g} "
+                    "warm-started from pass k-1; energy + fixed-point gradient; P^-1 g with delta = |g|^2, GMRES(30)",
+            "chi": w["chi"], "D": w["D"]}
+
+
 def metric_name(workload):
     return (f"hot-path passes/s ({workload}: warm-started CTMRG fixed point + energy + fixed-point "
             "gradient + local-metric GMRES(30) preconditioner per pass)")
@@ -337,14 +350,9 @@ def run_ours(args, rank, world, local):
         "dtype": {ipeps.FP64: "f64", ipeps.FP64_TC: "f64 from bf16 digits (tensor cores, fp32/int64 accumulate)",
                   ipeps.BF16X3: "bf16x3+f64", ipeps.TF32X3: "tf32x3+f64", ipeps.TF32X3_ALL: "tf32x3"}[prec],
         "data": "synthetic",
-        "config": {"workload": args.workload + (": Heisenberg square lattice 1x1, d=2, D=4, chi=64, Neel-like D=1 "
-                                                "seed in D=4 + 1e-2 noise (seed 0)" if args.workload == "heis_d4_chi64"
-                                                else ""),
-                   "pass": f"tensor_k = start + {PASS_EPS:g} U[-1,1] (seed {PASS_SEED}); CTMRG to "
-                           f"{PASS_TOL:g} warm-started from pass k-1; energy + fixed-point gradient; "
-                           "P^-1 g with delta = |g|^2, GMRES(30)",
-                   "precision": args.prec, "l2": "flushed (256 MB write) between timed passes",
-                   "parallelism": "replicas" if world > 1 else "single GPU", "chi": w["chi"], "D": w["D"]},
+        "config": dict(pass_config(args.workload), precision=args.prec,
+                       l2="flushed (256 MB write) between timed passes",
+                       parallelism="replicas" if world > 1 else "single GPU"),
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
         "ctmrg": {"iterations_per_pass": statistics.mean(ctm_its), "ms_per_pass": statistics.mean(ctm_ms),
                   "algorithmic_tflop_per_iteration": ctm_flops / 1e12,
@@ -467,7 +475,7 @@ def run_reference(args, rank, world):
     rec = {"impl": "reference", "metric": metric_name(args.workload), "value": v, "unit": "passes/s",
            "n_gpus": world, "steps": K, "warmup": W, "ms_per_step": 1e3 * t / K, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "precision": "fp64"},
+           "config": dict(pass_config(args.workload), precision="fp64 (oracle)", parallelism="host cores"),
            "cpu_baseline": {"value": v, "unit": "passes/s", "cores": cores, "kind": "oracle",
                             "sample": f"{K} timed oracle passes after {W} untimed ones (whole passes: CTMRG, "
                                       "energy, fixed-point gradient, preconditioner)"},
