@@ -408,20 +408,84 @@ def apply_signs(Lx, Ly, env, sig):
     return out
 
 
+def refine_gauge(Lx, Ly, env_ref, env_new, sig, sweeps=50):
+    """Orthogonal gauge G_b per chi bond (starting from the signs sig) with
+    env_ref ~ G . env_new elementwise, G acting on the first and last legs of
+    every boundary tensor: t'[i, ., j] = sum G_p[i, i'] t[i', ., j'] G_n[j, j'].
+
+    Needed when the projector spectra have exactly degenerate pairs (a
+    C4v-symmetric tensor gives them): a diagonal sign gauge cannot undo the
+    rotation inside a pair.  Alternating orthogonal Procrustes: with the other
+    bonds fixed, the overlap is linear in G_b (a bond that meets itself in an
+    edge uses its current value on the other side), maximised by the polar
+    factor of the accumulated overlap matrix."""
+    G = {b: np.diag(v).astype(np.float64) for b, v in sig.items()}
+    mats = []
+    for n in NAMES:
+        for x in range(Lx):
+            for y in range(Ly):
+                ref = _as3(env_ref[n][x][y].detach()).numpy()
+                new = _as3(env_new[n][x][y].detach()).numpy()
+                mats.append((bond_of(n, x, y, Lx, Ly), ref, new))
+    for _ in range(sweeps):
+        for b in list(G):
+            M = np.zeros_like(G[b])
+            for (bp, bn), ref, new in mats:
+                if bp == b:   # ref ~ G_b (new G_n^T): overlap with new on its last leg gauged
+                    X = np.einsum("imj,kj->imk", new, G[bn])
+                    M += np.einsum("imk,jmk->ij", ref, X)
+                if bn == b:   # ref ~ (G_p new) G_b^T
+                    Y = np.einsum("ki,imj->kmj", G[bp], new)
+                    M += np.einsum("kmi,kmj->ij", ref, Y)
+            u, _, vt = np.linalg.svd(M)
+            G[b] = u @ vt
+    return G
+
+
+def apply_gauge(Lx, Ly, env, G):
+    """t'[i, ., j] = sum G_p[i, i'] t[i', ., j'] G_n[j, j'] for every boundary tensor."""
+    out = {n: [[None] * Ly for _ in range(Lx)] for n in NAMES}
+    for n in NAMES:
+        for x in range(Lx):
+            for y in range(Ly):
+                bp, bn = bond_of(n, x, y, Lx, Ly)
+                t = env[n][x][y]
+                t3 = _as3(t)
+                gp = torch.as_tensor(G[bp], dtype=DT)
+                gn = torch.as_tensor(G[bn], dtype=DT)
+                out[n][x][y] = torch.einsum("ik,kmj,lj->iml", gp, t3, gn).reshape(t.shape)
+    return out
+
+
 def env_diff(Lx, Ly, e1, e2):
     return max(float(torch.linalg.norm(e1[n][x][y] - e2[n][x][y]))
                for n in NAMES for x in range(Lx) for y in range(Ly))
 
 
-def fixed_point(cell, chi, tol=1e-12, maxit=2000, env=None):
-    """CTMRG to convergence, then the sign gauge that makes the converged
-    environment an elementwise fixed point of one more iteration.
-    Returns (env*, sigma, spectral change, elementwise residual)."""
+def fixed_point(cell, chi, tol=1e-12, maxit=2000, env=None, gauge_refine_above=1e-8):
+    """CTMRG to convergence, then the gauge that makes the converged
+    environment an elementwise fixed point of one more iteration: the sign
+    gauge, refined to an orthogonal gauge (refine_gauge) when the sign gauge
+    leaves an elementwise residual above gauge_refine_above.
+    Returns (env*, gauge, iterations, spectral change, elementwise residual);
+    gauge is a dict of sign vectors or of orthogonal matrices (apply_fixed_gauge)."""
     Lx, Ly = len(cell), len(cell[0])
     env, it, err = ctmrg(cell, chi, tol=tol, maxit=maxit, env=env)
     A = as_torch_cell(cell)
     with torch.no_grad():
         e1 = ctmrg_step(Lx, Ly, A, env, chi)
-        sig = solve_signs(Lx, Ly, env, e1)
-        res = env_diff(Lx, Ly, env, apply_signs(Lx, Ly, e1, sig))
-    return env, sig, it, err, res
+        gauge = solve_signs(Lx, Ly, env, e1)
+        res = env_diff(Lx, Ly, env, apply_signs(Lx, Ly, e1, gauge))
+        if res > gauge_refine_above:
+            G = refine_gauge(Lx, Ly, env, e1, gauge)
+            res_g = env_diff(Lx, Ly, env, apply_gauge(Lx, Ly, e1, G))
+            if res_g < res:
+                gauge, res = G, res_g
+    return env, gauge, it, err, res
+
+
+def apply_fixed_gauge(Lx, Ly, env, gauge):
+    """Apply a gauge returned by fixed_point (signs or orthogonal matrices)."""
+    if next(iter(gauge.values())).ndim == 1:
+        return apply_signs(Lx, Ly, env, gauge)
+    return apply_gauge(Lx, Ly, env, gauge)

@@ -81,7 +81,7 @@ def energy_and_gradient(cell, ham, chi, tol=1e-12, maxit=2000, env=None, adj_tol
         e = _unflat_env(Lx, Ly, e_in)
         a = _unflat_A(Lx, Ly, a_in)
         e1 = C.ctmrg_step(Lx, Ly, a, e, chi)
-        e1 = C.apply_signs(Lx, Ly, e1, sig)
+        e1 = C.apply_fixed_gauge(Lx, Ly, e1, sig)
         return _flat_env(Lx, Ly, e1)
 
     def Efun(e_in, a_in):

@@ -30,8 +30,7 @@ def test_symmetry_group_and_projection():
     assert float((c4v.c4v_project(A) - A).abs().max()) < 1e-15
     for p in g:
         assert float((A.permute(*p) - A).abs().max()) < 1e-15
-    # a leg-only permutation leaves the physical leg alone: the projection of a
-    # tensor that is already symmetric in one reflection keeps its norm bound
+    # an orthogonal projection does not increase the norm
     B = torch.as_tensor(_sym_tensor(5, D=3))
     assert float(torch.linalg.norm(c4v.c4v_project(B))) <= float(torch.linalg.norm(B)) + 1e-12
 
@@ -110,3 +109,45 @@ def test_unrolled_gradient_reaches_the_converged_derivative():
         dlt = c4v.c4v_project(rng.normal(size=B.shape)).numpy()
         fd = (Egen(A + h * dlt) - Egen(A - h * dlt)) / (2 * h)
         assert abs(np.sum(g80 * dlt) - fd) < 1e-7 * abs(fd), (np.sum(g80 * dlt), fd)
+
+
+def test_fixed_point_gradient_at_a_c4v_tensor_needs_the_orthogonal_gauge():
+    # a C4v-symmetric tensor gives exactly degenerate pairs in the general
+    # CTMRG's projector spectra; the sign gauge alone leaves the environment
+    # off its elementwise fixed point, the orthogonal refinement restores it,
+    # and the implicit gradient then equals the unrolled C4v gradient along C4v
+    # directions and central differences along a non-symmetric one
+    from oracle import gradient as OG
+
+    B = _sym_tensor(0)
+    A = c4v.c4v_project(B).numpy()
+    chi = 8
+    env, gauge, it, err, res = OC.fixed_point([[A]], chi, tol=1e-11, maxit=3000)
+    assert next(iter(gauge.values())).ndim == 2 and res < 1e-10
+    with torch.no_grad():
+        e1 = OC.ctmrg_step(1, 1, OC.as_torch_cell([[A]]), env, chi)
+    signs = OC.solve_signs(1, 1, env, e1)
+    assert OC.env_diff(1, 1, env, OC.apply_signs(1, 1, e1, signs)) > 1e-6
+    E, g, info = OG.energy_and_gradient([[A]], HAM, chi, tol=1e-11, maxit=3000, return_info=True)
+    assert info["converged"] and info["fixed_point_residual"] < 1e-10
+    _, gu = c4v.energy_and_gradient(B, chi, HAM, n=60, N=80)
+    rng = np.random.default_rng(3)
+    dlt = c4v.c4v_project(rng.normal(size=B.shape)).numpy()
+    assert abs(np.sum(g[0][0] * dlt) - np.sum(gu * dlt)) < 1e-9 * abs(np.sum(gu * dlt))
+    dn = np.random.default_rng(4).normal(size=B.shape)
+    h = 1e-5
+
+    def Egen(Av):
+        e, _, er = OC.ctmrg([[Av]], chi, tol=1e-13, maxit=5000)
+        assert er < 1e-12
+        return float(OE.energy(1, 1, OC.as_torch_cell([[Av]]), e, HAM))
+
+    fd = (Egen(A + h * dn) - Egen(A - h * dn)) / (2 * h)
+    assert abs(np.sum(g[0][0] * dn) - fd) < 1e-6 * abs(fd)
+
+
+def test_random_tensor_keeps_the_sign_gauge():
+    rng = np.random.default_rng(9)
+    A = rng.uniform(-1, 1, (2, 2, 2, 2, 2))
+    env, gauge, it, err, res = OC.fixed_point([[A]], 8, tol=1e-11, maxit=3000)
+    assert next(iter(gauge.values())).ndim == 1 and res < 1e-8
