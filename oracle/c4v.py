@@ -46,6 +46,8 @@ import torch
 
 from .ctmrg import DT
 from .energy import energy as general_energy
+from .lbfgs import lbfgs
+from .metric import local_metric, precondition
 
 # the eight symmetries of the square as permutations of the virtual legs
 # (u, l, d, r) = axes (1, 2, 3, 4) of A[s, u, l, d, r]: the four rotations
@@ -167,3 +169,33 @@ def energy_and_gradient(B, chi, ham, n=3, N=20, env=None):
     E = general_energy(1, 1, [[A]], as_general_env(C, T, A.shape[1]), ham)
     E.backward()
     return float(E.detach()), Bt.grad.detach().numpy().copy()
+
+
+def optimize(B0, chi, ham, *, precond=True, maxiter=100, n=3, N=20, callback=None, stop=None):
+    """L-BFGS (m = 200, Hager-Zhang; oracle/lbfgs.py) on the free tensor B of
+    the C4v-symmetric iPEPS A = c4v_project(B), each evaluation the (n + N)-step
+    energy and its unrolled gradient from the traced start (Sec. IV.A), with
+    or without the local-metric preconditioner (Eq. equ:local_metric) of the
+    environment after the n + N steps, projected back onto the C4v subspace.
+    Returns (B, E, log)."""
+    shape = np.asarray(B0).shape
+    D = shape[1]
+
+    def fg(x, st):
+        B = x.reshape(shape)
+        E, g = energy_and_gradient(B, chi, ham, n=n, N=N)
+        if not np.isfinite(E):
+            return np.inf, None, st
+        return E, g.ravel(), {"B": B}
+
+    def pc(st, v, delta):
+        A = c4v_project(st["B"])
+        with torch.no_grad():
+            C, T = ctmrg(A, chi, n + N)
+            M = local_metric(as_general_env(C, T, D), A, 0, 0).numpy()
+        x, _ = precondition(M, v.reshape(shape), delta)
+        return c4v_project(x).numpy().ravel()
+
+    x, f, g, log = lbfgs(fg, np.asarray(B0, dtype=np.float64).ravel(), precond=pc if precond else None, m=200,
+                         maxiter=maxiter, callback=callback, stop=stop)
+    return x.reshape(shape), f, log
