@@ -408,7 +408,7 @@ def apply_signs(Lx, Ly, env, sig):
     return out
 
 
-def refine_gauge(Lx, Ly, env_ref, env_new, sig, sweeps=50):
+def refine_gauge(Lx, Ly, env_ref, env_new, sig, sweeps=400):
     """Orthogonal gauge G_b per chi bond (starting from the signs sig) with
     env_ref ~ G . env_new elementwise, G acting on the first and last legs of
     every boundary tensor: t'[i, ., j] = sum G_p[i, i'] t[i', ., j'] G_n[j, j'].
@@ -428,6 +428,7 @@ def refine_gauge(Lx, Ly, env_ref, env_new, sig, sweeps=50):
                 new = _as3(env_new[n][x][y].detach()).numpy()
                 mats.append((bond_of(n, x, y, Lx, Ly), ref, new))
     for _ in range(sweeps):
+        moved = 0.0
         for b in list(G):
             M = np.zeros_like(G[b])
             for (bp, bn), ref, new in mats:
@@ -438,7 +439,11 @@ def refine_gauge(Lx, Ly, env_ref, env_new, sig, sweeps=50):
                     Y = np.einsum("ki,imj->kmj", G[bp], new)
                     M += np.einsum("kmi,kmj->ij", ref, Y)
             u, _, vt = np.linalg.svd(M)
-            G[b] = u @ vt
+            Gb = u @ vt
+            moved = max(moved, float(np.max(np.abs(Gb - G[b]))))
+            G[b] = Gb
+        if moved < 1e-15:
+            break
     return G
 
 
