@@ -46,6 +46,7 @@ import torch
 
 from .ctmrg import DT
 from .energy import energy as general_energy
+from .bp import bp_precondition
 from .lbfgs import lbfgs
 from .metric import local_metric, precondition
 
@@ -175,8 +176,10 @@ def optimize(B0, chi, ham, *, precond=True, maxiter=100, n=3, N=20, callback=Non
     """L-BFGS (m = 200, Hager-Zhang; oracle/lbfgs.py) on the free tensor B of
     the C4v-symmetric iPEPS A = c4v_project(B), each evaluation the (n + N)-step
     energy and its unrolled gradient from the traced start (Sec. IV.A), with
-    or without the local-metric preconditioner (Eq. equ:local_metric) of the
-    environment after the n + N steps, projected back onto the C4v subspace.
+    the local-metric preconditioner (precond=True or "local": Eq.
+    equ:local_metric, from the environment after the n + N steps), the
+    mean-field one (precond="bp": oracle/bp.py, App. A) or none (False); the
+    preconditioned vector is projected back onto the C4v subspace.
     Returns (B, E, log)."""
     shape = np.asarray(B0).shape
     D = shape[1]
@@ -196,6 +199,12 @@ def optimize(B0, chi, ham, *, precond=True, maxiter=100, n=3, N=20, callback=Non
         x, _ = precondition(M, v.reshape(shape), delta)
         return c4v_project(x).numpy().ravel()
 
-    x, f, g, log = lbfgs(fg, np.asarray(B0, dtype=np.float64).ravel(), precond=pc if precond else None, m=200,
+    def pc_bp(st, v, delta):
+        A = c4v_project(st["B"]).numpy()
+        out, _, _ = bp_precondition([[A]], [[v.reshape(shape)]], delta)
+        return c4v_project(out[0][0]).numpy().ravel()
+
+    pcf = pc_bp if precond == "bp" else (pc if precond else None)
+    x, f, g, log = lbfgs(fg, np.asarray(B0, dtype=np.float64).ravel(), precond=pcf, m=200,
                          maxiter=maxiter, callback=callback, stop=stop)
     return x.reshape(shape), f, log
