@@ -169,3 +169,21 @@ def test_preconditioned_c4v_optimisation_reaches_table_one_energy():
     _, E, log = c4v.optimize(B0, chi, HAM, precond=True, maxiter=40,
                              stop=lambda k, f, g: np.linalg.norm(g) < 1e-8)
     assert abs(E - row["E_ref"]) < 1e-7, E
+
+
+def test_orthogonal_gauge_on_a_two_by_two_cell():
+    # four copies of one C4v tensor: the refined gauge makes the 2x2 environment
+    # an elementwise fixed point too, and every site's gradient is a quarter of
+    # the one-site gradient (same state, four tensors)
+    from oracle import gradient as OG
+
+    ham = OM.heisenberg(False)
+    A = c4v.c4v_project(_sym_tensor(0)).numpy()
+    cell = [[A, A], [A, A]]
+    E, g, info = OG.energy_and_gradient(cell, ham, 8, tol=1e-11, maxit=3000, return_info=True)
+    assert info["converged"] and info["fixed_point_residual"] < 1e-10
+    E1, g1 = OG.energy_and_gradient([[A]], ham, 8, tol=1e-11, maxit=3000)
+    assert abs(E - E1) < 1e-12
+    for x in range(2):
+        for y in range(2):
+            assert np.max(np.abs(g[x][y] - g1[0][0] / 4)) < 1e-12
