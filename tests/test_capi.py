@@ -118,3 +118,17 @@ def test_optimize_rejects_unknown_preconditioner_on_host(lib):
         sh = ipeps.Shape(1, 1, 2, D)
         st = L.ipeps_optimize(C.byref(sh), C.c_void_p(8), h.h, C.byref(o), ipeps.ITER_CB(0), None, None)
         assert st == 1 and b"bad options" in L.ipeps_last_error(), (pre, D)
+
+
+def test_public_header_is_plain_c():
+    # the boundary is a C ABI: the header compiles as C99 (and as C++) on its own
+    import os
+    import shutil
+    import subprocess
+
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ipeps.h")
+    for cc, args in (("gcc", ["-std=c99", "-x", "c"]), ("g++", ["-std=c++17", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not installed")
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Werror", *args, hdr], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
