@@ -136,11 +136,6 @@ def as_general_env(C, T, D):
     return {n: [[C if n[0] == "C" else T4]] for n in names}
 
 
-def corner_spectrum(C):
-    s = torch.linalg.svdvals(C)
-    return s / s.norm()
-
-
 def ctmrg(A, chi, steps, env=None):
     """`steps` symmetric CTMRG steps from env (or the traced start).  Returns (C, T)."""
     a = double_layer(A)
