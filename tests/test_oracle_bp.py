@@ -137,3 +137,16 @@ def test_messages_are_symmetric_psd_fixed_points():
         for lam in bp.LEGS:
             new = bp._normalise(bp._outgoing(cell[x][0], ins, lam))
             assert np.max(np.abs(new - msgs[(x, 0, lam)])) < 1e-11
+
+
+def test_c4v_symmetric_tensor_sends_equal_messages_on_all_legs():
+    # the eight symmetries of the square map the four legs onto each other, so a
+    # C4v-symmetric tensor's four outgoing messages coincide
+    from oracle import c4v
+
+    rng = np.random.default_rng(21)
+    A = c4v.c4v_project(rng.uniform(-1, 1, (2, 3, 3, 3, 3))).numpy()
+    msgs, it, ch = bp.bp_messages([[A]])
+    assert ch <= 1e-12
+    for lam in ("l", "d", "r"):
+        assert np.max(np.abs(msgs[(0, 0, lam)] - msgs[(0, 0, "u")])) < 1e-12
