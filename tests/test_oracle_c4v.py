@@ -153,10 +153,11 @@ def test_random_tensor_keeps_the_sign_gauge():
     assert next(iter(gauge.values())).ndim == 1 and res < 1e-8
 
 
-def test_preconditioned_c4v_optimisation_reaches_table_one_energy():
-    # end to end: C4v CTMRG (3 + 20 steps), unrolled gradient, local-metric
-    # preconditioned L-BFGS from a seeded random C4v tensor reach the D=2,
-    # chi=32 reference energy the paper prints (Table I, seven digits)
+@pytest.mark.parametrize("precond", [True, "bp"])
+def test_preconditioned_c4v_optimisation_reaches_table_one_energy(precond):
+    # end to end: C4v CTMRG (3 + 20 steps), unrolled gradient, local-metric (or
+    # mean-field) preconditioned L-BFGS from a seeded random C4v tensor reach
+    # the D=2, chi=32 reference energy the paper prints (Table I, seven digits)
     import json
     import os
 
@@ -166,7 +167,7 @@ def test_preconditioned_c4v_optimisation_reaches_table_one_energy():
     rng = np.random.default_rng(0)
     B0 = c4v.c4v_project(rng.uniform(-1, 1, (2, D, D, D, D))).numpy()
     B0 /= np.abs(B0).max()
-    _, E, log = c4v.optimize(B0, chi, HAM, precond=True, maxiter=40,
+    _, E, log = c4v.optimize(B0, chi, HAM, precond=precond, maxiter=40,
                              stop=lambda k, f, g: np.linalg.norm(g) < 1e-8)
     assert abs(E - row["E_ref"]) < 1e-7, E
 
